@@ -1,0 +1,503 @@
+"""CPU FP64 oracle for gradient-type subspace iteration (Alimisis, Saad &
+Vandereycken, arXiv 2306.10379).
+
+TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the
+CPU-baseline leg of the benchmark may import this module. The CUDA library
+never calls it, shares no code with it, and must fail loudly rather than fall
+back to it.
+
+Plain, slow and direct: numpy / scipy.sparse library products serve as the
+matrix products, numpy.linalg.eigh as the small symmetric eigensolver, and
+everything else is written out in the order of the paper's algorithms. All
+arithmetic is float64.
+
+Sign convention. The paper writes G = grad phi = -(AX - XC) and steps
+X - mu*G (Sec. 3, Eq. (gradPhi), Alg. 2). Here R = AX - XC (the residual,
+= -G) and the step is X + t*D with t >= 0; the iterates are identical. With
+this sign zeta_i = (V^T D^T A X V)_ii = (V^T D^T R V)_ii for tangent D (the
+paper's D_zeta of Eq. (CG_linesearch_D) after the sign flip), and
+zeta = beta for steepest descent (Eqs. (GTAY)-(GTG)).
+
+Readings of points the paper leaves open (each is listed in the design doc):
+  * stopping test ||R||_F / ||A||_2 <= tol, checked every iteration;
+  * Brent-Dekker root finding on phi'(t) with tolerance 2 eps |t|, at most
+    100 evaluations;
+  * branches with beta_i <= eps * sum(beta) and, for CG, the concave branches
+    (zeta_i <= 0) are left out of the bracket but kept in phi';
+  * the step is the first minimiser of the model past xi_min: the bracket's
+    right end is found by doubling from xi_min (capped at xi_max), lo <- 0
+    when phi'(xi_min) > 0;
+  * CG: first iteration and restarts use P = R; plain Polak-Ribiere beta;
+    restart when <P, R> <= 0 or every k_restart iterations (0 = never);
+  * zeta is taken from D^T R, and the polar factor from the measured Gram of
+    X + tD (both equal the paper's expressions in exact arithmetic);
+  * AX is recomputed explicitly when t*sqrt(beta_max) < 1e3*eps, every
+    `recompute_every` iterations, and before the final residual.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+EPS = np.finfo(np.float64).eps
+
+
+# ---------------------------------------------------------------------------
+# Operator and block products (Sec. 6.1, "Efficient matvecs")
+# ---------------------------------------------------------------------------
+
+def csr_operator(n, rowptr, colidx, val):
+    """scipy CSR matrix from plain CSR arrays."""
+    return sp.csr_matrix((np.asarray(val, np.float64), np.asarray(colidx, np.int64),
+                          np.asarray(rowptr, np.int64)), shape=(n, n))
+
+
+def spmm(A, X):
+    """Block matvec W = A X (one per iteration in the paper's accounting)."""
+    return np.asarray(A @ X)
+
+
+def gram(U, V):
+    """Tall-skinny Gram product U^T V (p x p)."""
+    return U.T @ V
+
+
+def residual(X, Y, C):
+    """R = AX - XC with Y = AX and C = X^T A X (Eq. (gradPhi), sign flipped)."""
+    return Y - X @ C
+
+
+def anorm_inf(A):
+    """||A||_inf = max absolute row sum, an upper bound of ||A||_2."""
+    return float(np.max(np.asarray(abs(A).sum(axis=1)).ravel()))
+
+
+# ---------------------------------------------------------------------------
+# Line search (Sec. 3.1 Eqs. (Gdec)-(xii), Sec. 5.2 Eqs. (phi_P)-(deriv_P),
+# Sec. 6.1 Eqs. (derv1)-(derv2), Alg. 3)
+# ---------------------------------------------------------------------------
+
+def ls_coefficients(C, B, Gamma, Z):
+    """Diagonalise B = D^T D = V diag(beta) V^T (Eq. (Gdec)) and return
+    alpha = diag(V^T C V), beta, gamma = diag(V^T Gamma V),
+    zeta = diag(V^T Z V) (Eqs. (diags), (CG_linesearch_D)), and V."""
+    Bs = 0.5 * (B + B.T)
+    beta, V = np.linalg.eigh(Bs)
+    beta = np.maximum(beta, 0.0)
+    alpha = np.einsum("ki,kl,li->i", V, C, V)
+    gamma = np.einsum("ki,kl,li->i", V, Gamma, V)
+    zeta = np.einsum("ki,kl,li->i", V, Z, V)
+    return alpha, beta, gamma, zeta, V
+
+
+def phi_model(t, alpha, beta, gamma, zeta):
+    """phi(X(t)) = -1/2 sum (alpha_i + 2 zeta_i t + gamma_i t^2)/(1 + beta_i t^2),
+    Eq. (phi_P) (Eq. (phinew) when zeta = beta)."""
+    return -0.5 * float(np.sum((alpha + 2.0 * zeta * t + gamma * t * t) / (1.0 + beta * t * t)))
+
+
+def dphi_model(t, alpha, beta, gamma, zeta):
+    """phi'(t) = -sum (zeta_i + (gamma_i - alpha_i beta_i) t - beta_i zeta_i t^2)
+    / (1 + beta_i t^2)^2, Eq. (deriv_P) (Eq. (dqnew) when zeta = beta).
+    The sum runs over i in ascending order."""
+    num = zeta + (gamma - alpha * beta) * t - beta * zeta * t * t
+    den = (1.0 + beta * t * t) ** 2
+    return -float(np.sum(num / den))
+
+
+def branch_roots(alpha, beta, gamma, zeta):
+    """Positive root xi_i of each bracket-eligible branch numerator
+    zeta_i + delta_i t - beta_i zeta_i t^2, delta_i = gamma_i - alpha_i beta_i,
+    in the cancellation-free forms of Eqs. (derv1) (delta_i < 0) and (derv2)
+    (delta_i >= 0), written with zeta_i in place of beta_i where the CG
+    generalisation puts it. Eligible: beta_i > eps*sum(beta) and zeta_i > 0
+    (concave branches are ignored for the bracket, Sec. 5.2)."""
+    sb = float(np.sum(beta))
+    xs = []
+    for a, b, g, z in zip(alpha, beta, gamma, zeta):
+        if not (b > EPS * sb) or not (z > 0.0):
+            continue
+        d = g - a * b
+        disc = math.sqrt(d * d + 4.0 * b * z * z)
+        if d < 0.0:
+            xs.append(2.0 * z / (-d + disc))
+        else:
+            xs.append((d + disc) / (2.0 * b * z))
+    return np.array(xs)
+
+
+def brent_zero(f, a, b, fa, fb, maxeval=100):
+    """Dekker-Brent safeguarded root finder (R. P. Brent, Algorithms for
+    Minimization without Derivatives, 1973, ch. 4), for f(a) f(b) <= 0.
+
+    Keeps a bracket [b, c] with f(b) f(c) <= 0 and |f(b)| <= |f(c)|, tries
+    inverse quadratic interpolation (secant with two points) and accepts it
+    only while it stays inside the bracket and shrinks fast enough; otherwise
+    bisects. Stops when the bracket half-width is below 2 eps |b| (+ tiny).
+    Returns (root, evaluations)."""
+    evals = 0
+    if fa == 0.0:
+        return a, evals
+    if fb == 0.0:
+        return b, evals
+    c, fc = a, fa
+    e = d = b - a
+    while evals < maxeval:
+        if (fb > 0.0 and fc > 0.0) or (fb < 0.0 and fc < 0.0):
+            c, fc = a, fa
+            e = d = b - a
+        if abs(fc) < abs(fb):
+            a, b, c = b, c, b
+            fa, fb, fc = fb, fc, fb
+        tol = 2.0 * EPS * abs(b) + 1e-300
+        m = 0.5 * (c - b)
+        if abs(m) <= tol or fb == 0.0:
+            break
+        if abs(e) >= tol and abs(fa) > abs(fb):
+            s = fb / fa
+            if a == c:
+                pq_p = 2.0 * m * s
+                pq_q = 1.0 - s
+            else:
+                q = fa / fc
+                r = fb / fc
+                pq_p = s * (2.0 * m * q * (q - r) - (b - a) * (r - 1.0))
+                pq_q = (q - 1.0) * (r - 1.0) * (s - 1.0)
+            if pq_p > 0:
+                pq_q = -pq_q
+            else:
+                pq_p = -pq_p
+            if 2.0 * pq_p < min(3.0 * m * pq_q - abs(tol * pq_q), abs(e * pq_q)):
+                e, d = d, pq_p / pq_q
+            else:
+                d = e = m
+        else:
+            d = e = m
+        a, fa = b, fb
+        b = b + d if abs(d) > tol else b + math.copysign(tol, m)
+        fb = f(b)
+        evals += 1
+    return b, evals
+
+
+def get_mu(alpha, beta, gamma, zeta, max_doublings=64):
+    """Alg. 3 (Get_Mu), generalised to zeta for CG (Sec. 5.2).
+
+    phi' < 0 on [0, xi_min] (every eligible branch still descends), so the
+    search starts at xi_min. The bracket's right end is found by doubling from
+    xi_min (capped at xi_max on the first pass) until phi' >= 0, and Brent then
+    finds the root of phi' in [lo, hi]: the first local minimiser of the
+    model past xi_min. A branch whose beta_i sits at rounding level has no
+    relative accuracy and can put a spurious root of phi' far beyond the main
+    minimum; stopping at the first sign change keeps the step where the model
+    is accurate. If phi'(xi_min) > 0 (possible for CG) the search runs on
+    [0, xi_min]; if phi'(0) >= 0 the direction is not a descent direction and
+    t = 0. Returns (t, evaluations, lo, hi)."""
+    xs = branch_roots(alpha, beta, gamma, zeta)
+    if xs.size == 0:
+        return 0.0, 0, 0.0, 0.0
+    f = lambda t: dphi_model(t, alpha, beta, gamma, zeta)
+    xmin, xmax = float(xs.min()), float(xs.max())
+    fa = f(xmin)
+    evals = 1
+    if fa > 0.0:
+        lo, flo = 0.0, f(0.0)
+        evals += 1
+        if flo >= 0.0:
+            return 0.0, evals, 0.0, xmin
+        hi, fhi = xmin, fa
+    else:
+        lo, flo = xmin, fa
+        hi, fhi = xmin, fa
+        k = 0
+        while fhi < 0.0:
+            if k >= max_doublings:
+                return hi, evals, lo, hi
+            nxt = 2.0 * hi
+            if hi < xmax:
+                nxt = min(nxt, xmax)
+            lo, flo = hi, fhi
+            hi = nxt
+            fhi = f(hi)
+            evals += 1
+            k += 1
+    t, ev = brent_zero(f, lo, hi, flo, fhi)
+    return t, evals + ev, lo, hi
+
+
+def polar_factor_matrix(V, beta, t):
+    """M = V (I + t^2 D_beta)^{-1/2} V^T, so that (X + tD) M is the polar
+    factor of X + tD (Eqs. (Psi3), (Ynew), (Xnew_P))."""
+    d = 1.0 / np.sqrt(1.0 + t * t * beta)
+    return (V * d) @ V.T
+
+
+def inverse_sqrt(S):
+    """S^{-1/2} of a symmetric positive definite p x p matrix (eigh).
+
+    The retraction uses M = (Z^T Z)^{-1/2} with Z = X + tD and the Gram
+    Z^T Z measured, so that Z M is the polar factor of Z (Eq. (Ynew)). In
+    exact arithmetic Z^T Z = I + t^2 D^T D and M = V D_t^{-1} V^T; in floating
+    point the measured Gram keeps X orthonormal, while the analytic form lets
+    ||X^T X - I|| grow by about |1 - 2 t lambda| per step (the residual
+    R = Y - XC is tangent only up to (X^T X - I) C)."""
+    s, U = np.linalg.eigh(0.5 * (S + S.T))
+    return (U / np.sqrt(s)) @ U.T
+
+
+# ---------------------------------------------------------------------------
+# Start block, Rayleigh-Ritz, diagnostics
+# ---------------------------------------------------------------------------
+
+def orthonormalize(X0):
+    """Polar orthonormalisation X0 (X0^T X0)^{-1/2}, applied twice (the second
+    pass removes the rounding left by the first), via eigh of the Gram."""
+    X = np.array(X0, dtype=np.float64)
+    for _ in range(2):
+        s, U = np.linalg.eigh(X.T @ X)
+        X = X @ ((U / np.sqrt(s)) @ U.T)
+    return X
+
+
+def rayleigh_ritz(X, Y):
+    """Ritz pairs of span(X) with Y = AX: C = X^T Y = U diag(theta) U^T,
+    Ritz vectors XU, values theta in descending order (Eq. (rr1))."""
+    C = X.T @ Y
+    theta, U = np.linalg.eigh(0.5 * (C + C.T))
+    order = np.argsort(theta)[::-1]
+    return theta[order], X @ U[:, order], U[:, order]
+
+
+def principal_angles(X, U):
+    """Principal angles between span(X) and span(U), both orthonormal: the
+    cosines are the singular values of X^T U."""
+    s = np.linalg.svd(X.T @ U, compute_uv=False)
+    return np.arccos(np.clip(s, -1.0, 1.0))
+
+
+# ---------------------------------------------------------------------------
+# Riemannian steepest descent (Alg. 2) and conjugate gradients (Alg. 4)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Options:
+    method: str = "sd"              # "sd" (Alg. 2) or "cg" (Alg. 4)
+    tol: float = 1e-8               # on ||R||_F / anorm
+    anorm: float = 0.0              # 0 -> ||A||_inf
+    max_iters: int = 10000
+    k_restart: int = 0              # 0 = never
+    recompute_every: int = 50
+    explicit_ax: bool = False       # RCG(+): explicit AX every iteration
+
+
+@dataclass
+class IterRecord:
+    k: int
+    t: float
+    phi: float
+    res_f: float
+    res_inf: float
+    evals: int
+    restarted: bool
+
+
+@dataclass
+class Result:
+    X: np.ndarray
+    Y: np.ndarray
+    iters: int
+    matvecs: int
+    converged: bool
+    rel_residual: float
+    restarts: int
+    history: list = field(default_factory=list)
+
+
+def solve(A, X0, opts: Options, record=False, callback=None):
+    """Run Alg. 2 (opts.method == "sd") or Alg. 4 ("cg") from X0.
+
+    Per iteration k (all quantities float64):
+      R = Y - X C, C = X^T Y                          (Eq. (gradPhi))
+      stop if ||R||_F <= tol * anorm
+      D = R (SD); CG: D = R + beta_PR (P - X (X^T P)) (Eq. (Pnew) with the
+          projection transport), restart to D = R when <D, R> <= 0 or every
+          k_restart iterations
+      W = A D                                          (the one block matvec)
+      B = D^T D, Gamma = D^T W, Z = D^T R (= D^T A X for tangent D, the
+          identity used in Sec. 5.2; Z = B for SD by Eqs. (GTAY)-(GTG)). D^T Y
+          itself would carry (D^T X) C, a rounding-level term that swamps
+          <D, R> once ||R|| < sqrt(eps) ||A||
+      t = Get_Mu(alpha, beta, gamma, zeta)             (Alg. 3)
+      M = (Z^T Z)^{-1/2}, Z = X + tD, the polar factor  (Eq. (Ynew), Eq. (Xnew_P))
+      X <- Z M,  Y <- (Y + tW) M                       (Eq. (save_matvec))
+    """
+    n, p = X0.shape
+    anorm = opts.anorm if opts.anorm > 0 else anorm_inf(A)
+    X = orthonormalize(X0)
+    Y = spmm(A, X)
+    matvecs = 1
+    P = None
+    R_prev = None
+    rr_prev = None
+    restarts = 0
+    history = []
+    res0_inf = None
+    converged = False
+    y_fresh = True
+    k = 0
+    rel = float("nan")
+    while True:
+        C = gram(X, Y)
+        C = 0.5 * (C + C.T)
+        R = residual(X, Y, C)
+        rr = float(np.sum(R * R))
+        rel = math.sqrt(rr) / anorm
+        res_inf = float(np.max(np.sum(np.abs(R), axis=1)))
+        if res0_inf is None:
+            res0_inf = res_inf
+        if rel <= opts.tol or k >= opts.max_iters:
+            if not y_fresh:
+                # the final residual is always taken with an explicit AX
+                Y = spmm(A, X)
+                matvecs += 1
+                y_fresh = True
+                continue
+            converged = rel <= opts.tol
+            break
+        restarted = False
+        if opts.method == "sd" or P is None:
+            D = R
+        else:
+            beta_pr = (rr - float(np.sum(R * R_prev))) / rr_prev
+            Kp = gram(X, P)
+            D = R + beta_pr * (P - X @ Kp)
+            due = opts.k_restart > 0 and k % opts.k_restart == 0
+            if due or float(np.sum(D * R)) <= 0.0:
+                D = R
+                restarted = True
+        if restarted:
+            restarts += 1
+        W = spmm(A, D)
+        matvecs += 1
+        B = gram(D, D)
+        Gam = gram(D, W)
+        Z = B if opts.method == "sd" else gram(D, R)
+        alpha, beta, gamma, zeta, V = ls_coefficients(C, B, 0.5 * (Gam + Gam.T), Z)
+        t, evals, _, _ = get_mu(alpha, beta, gamma, zeta)
+        Zt = X + t * D
+        M = inverse_sqrt(gram(Zt, Zt))
+        X = Zt @ M
+        recompute = (opts.explicit_ax or t * math.sqrt(max(beta.max(), 0.0)) < 1e3 * EPS
+                     or (opts.recompute_every > 0 and (k + 1) % opts.recompute_every == 0))
+        if recompute:
+            Y = spmm(A, X)
+            matvecs += 1
+        else:
+            Y = (Y + t * W) @ M
+        y_fresh = recompute
+        if record:
+            history.append(IterRecord(k, t, phi_model(t, alpha, beta, gamma, zeta),
+                                      math.sqrt(rr), res_inf / res0_inf, evals, restarted))
+        if callback is not None:
+            callback(k, X, Y, t)
+        P, R_prev, rr_prev = D, R, rr
+        k += 1
+    return Result(X, Y, k, matvecs, converged, rel, restarts, history)
+
+
+# ---------------------------------------------------------------------------
+# Chebyshev-filtered subspace iteration (Alg. 1 with Eq. (optimal_poly))
+# ---------------------------------------------------------------------------
+
+def chebyshev_filter(A, X, degree, c, h, scale_at):
+    """Z = C_d((A - cI)/h) X / C_d((scale_at - c)/h) by the three-term
+    recurrence T_{k+1} = 2 s T_k - T_{k-1}, s = (A - cI)/h, with each step
+    divided by the running scale ratio so the top of the spectrum stays O(1)
+    (the scaling at lambda_1 of Sec. 2.2)."""
+    e = (scale_at - c) / h
+    sigma = 1.0 / e
+    Z_prev = X
+    Z = (spmm(A, X) - c * X) * (sigma / h)
+    for _ in range(1, degree):
+        sigma_next = 1.0 / (2.0 * e - sigma)
+        Z_next = (2.0 * sigma_next / h) * (spmm(A, Z) - c * Z) - (sigma * sigma_next) * Z_prev
+        Z_prev, Z, sigma = Z, Z_next, sigma_next
+    return Z
+
+
+def chebyshev_si(A, X0, degree, lam_p1, lam_n, lam_1, tol=1e-8, anorm=0.0, max_outer=10000):
+    """Alg. 1 with p_k = C_d((t - c)/h), c = (lam_{p+1} + lam_n)/2,
+    h = (lam_{p+1} - lam_n)/2, scaled at lam_1 (Eq. (optimal_poly)); an
+    orthonormalisation and Rayleigh-Ritz after every `degree` matvecs.
+    Returns (X, theta, outer iterations, matvecs, rel residual)."""
+    anorm = anorm if anorm > 0 else anorm_inf(A)
+    c = 0.5 * (lam_p1 + lam_n)
+    h = 0.5 * (lam_p1 - lam_n)
+    X = orthonormalize(X0)
+    matvecs = 0
+    rel = float("nan")
+    for outer in range(max_outer + 1):
+        Y = spmm(A, X)
+        matvecs += 1
+        theta, Xr, U = rayleigh_ritz(X, Y)
+        Yr = Y @ U
+        R = Yr - Xr * theta
+        rel = float(np.linalg.norm(R)) / anorm
+        X = Xr
+        if rel <= tol or outer == max_outer:
+            return X, theta, outer, matvecs, rel
+        Z = chebyshev_filter(A, X, degree, c, h, lam_1)
+        matvecs += degree
+        Q, _ = np.linalg.qr(Z)
+        X = Q
+    return X, theta, max_outer, matvecs, rel
+
+
+# ---------------------------------------------------------------------------
+# SELL-C-sigma (sliced ELLPACK) layout of a CSR matrix
+# ---------------------------------------------------------------------------
+
+def sell_c_sigma(n, rowptr, colidx, val, C=32, sigma=32):
+    """Sliced ELLPACK with chunk height C and sorting window sigma.
+
+    Within each window of sigma consecutive rows, rows are ordered by nnz
+    descending, ties by ascending row index. Consecutive groups of C permuted
+    rows form a chunk whose width is its longest row; chunk storage is
+    column-major (entry j of the C rows, then entry j+1, ...). Padding slots
+    hold the row's own index as column and 0.0 as value; rows past n in the
+    last chunk are padding rows with perm = -1.
+    Returns (perm, chunk_ptr, chunk_len, sell_col, sell_val):
+    perm[k] = original row at permuted position k."""
+    rowptr = np.asarray(rowptr, np.int64)
+    lens = np.diff(rowptr)
+    perm = []
+    for w0 in range(0, n, sigma):
+        rows = list(range(w0, min(n, w0 + sigma)))
+        rows.sort(key=lambda r: (-int(lens[r]), r))
+        perm.extend(rows)
+    nchunks = (n + C - 1) // C
+    perm = perm + [-1] * (nchunks * C - n)
+    chunk_len = np.zeros(nchunks, np.int64)
+    for ch in range(nchunks):
+        rows = [r for r in perm[ch * C:(ch + 1) * C] if r >= 0]
+        chunk_len[ch] = max(int(lens[r]) for r in rows)
+    chunk_ptr = np.zeros(nchunks + 1, np.int64)
+    chunk_ptr[1:] = np.cumsum(chunk_len * C)
+    scol = np.zeros(int(chunk_ptr[-1]), np.int32)
+    sval = np.zeros(int(chunk_ptr[-1]), np.float64)
+    for ch in range(nchunks):
+        base = int(chunk_ptr[ch])
+        for lane in range(C):
+            r = perm[ch * C + lane]
+            for j in range(int(chunk_len[ch])):
+                slot = base + j * C + lane
+                if r >= 0 and j < lens[r]:
+                    scol[slot] = colidx[rowptr[r] + j]
+                    sval[slot] = val[rowptr[r] + j]
+                else:
+                    scol[slot] = max(r, 0) if r >= 0 else 0
+                    sval[slot] = 0.0
+    return np.array(perm, np.int64), chunk_ptr, chunk_len, scol, sval
