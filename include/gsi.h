@@ -1,0 +1,201 @@
+/*
+ * gsi.h -- C ABI of the GB300 (sm_103a) library for gradient-type subspace
+ * iteration: Riemannian steepest descent and conjugate gradients with exact
+ * line search for the dominant p-dimensional invariant subspace of a real
+ * symmetric matrix A (Alimisis, Saad & Vandereycken, arXiv 2306.10379).
+ *
+ * Problem statement (Sec. 1 and Sec. 2.1): minimise
+ * phi(X) = -1/2 tr(X^T A X) over n x p matrices with X^T X = I; the minimiser
+ * spans the eigenvectors of the p largest eigenvalues (the smallest ones are
+ * obtained from -A). Each iteration runs Alg. 2 (SD) or Alg. 4 (CG) with the
+ * exact line search of Alg. 3 and the one-matvec recursion of Eq.
+ * (save_matvec).
+ *
+ * Conventions shared by every entry point:
+ *  - Dense n x p blocks are row-major (the p entries of a row contiguous),
+ *    float64. p x p matrices are row-major float64.
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device; "host" pointers are ordinary host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is stream-ordered; entry points that return results in
+ *    host memory synchronise that stream before returning.
+ *  - No entry point throws; each returns a gsi_status. On GSI_ERR_ARG nothing
+ *    was launched. On GSI_ERR_CUDA the CUDA error string is available from
+ *    gsi_last_error().
+ *  - Contexts are not thread-safe; distinct contexts are independent.
+ */
+#ifndef GSI_H
+#define GSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GSI_OK = 0,
+  GSI_ERR_ARG = 1,        /* invalid argument (sizes, null pointers, p range) */
+  GSI_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  GSI_ERR_OOM = 3,        /* device allocation failed */
+  GSI_ERR_NOCONV = 4,     /* max_iters reached before the tolerance */
+  GSI_ERR_BREAKDOWN = 5,  /* a p x p factorisation broke down (rank-deficient block) */
+  GSI_ERR_NONFINITE = 6,  /* NaN or Inf met in the iteration */
+  GSI_ERR_TIMEOUT = 7     /* a bounded device-side wait expired */
+} gsi_status;
+
+typedef enum { GSI_CSR = 0, GSI_SELL = 1 } gsi_format;
+typedef enum { GSI_SD = 0, GSI_CG = 1 } gsi_method;
+
+/* Sparse symmetric A in full CSR storage (both triangles).
+ * rowptr: n+1 int64, colidx: nnz int32 (0-based), val: nnz float64.
+ * on_device = 0: the three arrays are host memory; 1: device memory.
+ * fmt = GSI_SELL asks the context to convert A to SELL-C-sigma
+ * (chunk height sell_C = 32, sorting window sell_sigma) for its SpMM.
+ * Symmetry is not checked. */
+typedef struct {
+  int32_t fmt;
+  int64_t n;
+  int64_t nnz;
+  const int64_t* rowptr;
+  const int32_t* colidx;
+  const double* val;
+  int32_t sell_C;
+  int32_t sell_sigma;
+  int32_t on_device;
+} gsi_matrix;
+
+typedef struct {
+  int32_t method;          /* GSI_SD (Alg. 2) or GSI_CG (Alg. 4) */
+  int32_t which;           /* +1: largest p eigenvalues; -1: smallest (runs on -A) */
+  double tol;              /* stop when ||R||_F / anorm <= tol (default 1e-8) */
+  double anorm;            /* ||A||_2 or an upper bound; <= 0: ||A||_inf is used */
+  int32_t max_iters;       /* default 10000 */
+  int32_t k_restart;       /* CG restart period; 0 = never (default) */
+  int32_t recompute_every; /* explicit Y = AX every k iterations; 0 = only when the step is tiny */
+  int32_t explicit_ax;     /* 1: explicit AX every iteration ("RCG(+)", Sec. 6.4) */
+} gsi_opts;
+
+typedef struct {
+  int32_t iters;           /* iterations done since gsi_create */
+  int32_t matvecs;         /* block matvecs A*Z done since gsi_create */
+  int32_t restarts;        /* CG restarts to the gradient direction */
+  int32_t brent_evals;     /* phi' evaluations in the last line search */
+  int32_t converged;       /* 1 once ||R||_F / anorm <= tol with an explicit AX */
+  double rel_residual;     /* ||R||_F / anorm at the last check */
+  double rel_residual_inf; /* ||R||_inf / ||R_0||_inf (the paper's table criterion) */
+  double trace;            /* tr(X^T A X) at the last check (sign as for A, not -A) */
+  double last_step;        /* step t of the last line search */
+} gsi_info;
+
+typedef struct gsi_ctx gsi_ctx;
+
+/* Fill *o with the defaults listed above. */
+gsi_status gsi_default_opts(gsi_opts* o);
+
+/* Create a solver context on the current device.
+ * A: the operator (copied into library-owned device memory; the caller keeps
+ *    its arrays). p: block size, 1 <= p <= 128 and n >= 2p.
+ * X0: n x p start block (need not be orthonormal); X0_on_device selects host
+ *    or device memory. It is copied and orthonormalised by the polar factor
+ *    X0 (X0^T X0)^{-1/2}, applied twice.
+ * stream: the stream all work of this context is ordered on.
+ * Returns GSI_ERR_BREAKDOWN if X0 is numerically rank deficient. */
+gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t X0_on_device,
+                      const gsi_opts* o, void* stream, gsi_ctx** out);
+
+/* Run at most nsteps iterations (stops early on convergence); info may be NULL.
+ * Returns GSI_OK (also when converged), or an error status. */
+gsi_status gsi_step(gsi_ctx* ctx, int32_t nsteps, gsi_info* info);
+
+/* Iterate until ||R||_F/anorm <= tol (checked with an explicit AX) or
+ * max_iters; GSI_ERR_NOCONV in the latter case, with info filled and the
+ * basis retrievable. */
+gsi_status gsi_solve(gsi_ctx* ctx, gsi_info* info);
+
+/* Current basis. X: n x p (may be NULL); evals: p Ritz values of A (may be
+ * NULL; computed by a Rayleigh-Ritz step with an explicit AX, Eq. (rr1),
+ * which also rotates the returned X to the Ritz vectors; descending for
+ * which = +1, ascending -- smallest first -- for which = -1, in the order of
+ * the columns of X). to_device: 1 if X and evals are device pointers, 0 for
+ * host. The context's own iterate is not changed. */
+gsi_status gsi_get_basis(gsi_ctx* ctx, double* X, double* evals, int32_t to_device);
+
+/* Device pointers of the context's current iterate X and Y = AX (n x p
+ * row-major), valid until the next call on ctx. For tests and benchmarks. */
+gsi_status gsi_state_ptrs(gsi_ctx* ctx, double** X, double** Y);
+
+gsi_status gsi_destroy(gsi_ctx* ctx);
+
+const char* gsi_status_str(gsi_status s);
+/* Text of the last CUDA error seen by this library (thread-local). */
+const char* gsi_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Kernel-level entry points. All pointers are device pointers unless noted.
+ * They expose the steps of one iteration for parity tests and benchmarks.
+ * ---------------------------------------------------------------------- */
+
+/* One block matvec W = A X (Sec. 6.1, "Efficient matvecs"): CSR A (n rows),
+ * X and W n x p. */
+gsi_status gsi_spmm_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                        const double* val, int32_t p, const double* X, double* W,
+                        void* stream);
+
+/* SELL-C-sigma layout of a CSR matrix, built on the host (all pointers host).
+ * Rows are sorted by nnz descending (ties: ascending row index) inside each
+ * window of sigma rows; chunks of C consecutive permuted rows are stored
+ * column-major with the chunk's longest row as width; padding entries have
+ * column = own row (0 for padding rows) and value 0.
+ * Query sizes with gsi_sell_size(), then fill:
+ *   perm[nchunks*C] (original row of each permuted slot, -1 = padding),
+ *   chunk_ptr[nchunks+1] (start of each chunk in the entry arrays),
+ *   chunk_len[nchunks], sell_col[total], sell_val[total]. */
+gsi_status gsi_sell_size(int64_t n, const int64_t* rowptr, int32_t C, int32_t sigma,
+                         int64_t* nchunks, int64_t* total);
+gsi_status gsi_csr_to_sell(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                           const double* val, int32_t C, int32_t sigma, int64_t* perm,
+                           int64_t* chunk_ptr, int64_t* chunk_len, int32_t* sell_col,
+                           double* sell_val);
+
+/* W = A X with A in SELL-C-sigma (device arrays from gsi_csr_to_sell).
+ * W rows are written at their original (unpermuted) positions. */
+gsi_status gsi_spmm_sell(int64_t n, int64_t nchunks, int32_t C, const int64_t* perm,
+                         const int64_t* chunk_ptr, const int64_t* chunk_len,
+                         const int32_t* sell_col, const double* sell_val, int32_t p,
+                         const double* X, double* W, void* stream);
+
+/* Tall-skinny Gram G = U^T V (Eq. (gradPhi) C = X^T A X; Eqs. (diags),
+ * (CG_linesearch_D)); U n x p, V n x q (row-major), G p x q.
+ * Uses a temporary device buffer for per-block partial sums (stream-ordered
+ * allocation on `stream`). */
+gsi_status gsi_gram(int64_t n, int32_t p, int32_t q, const double* U, const double* V,
+                    double* G, void* stream);
+
+/* Residual R = Y - X C (Eq. (gradPhi), sign flipped: R = -grad phi);
+ * X, Y, R n x p, C p x p. R may alias Y. */
+gsi_status gsi_residual(int64_t n, int32_t p, const double* X, const double* Y,
+                        const double* C, double* R, void* stream);
+
+/* The p x p part of one iteration (Alg. 3 and Eqs. (Gdec)-(xii), (phi_P),
+ * (deriv_P), (derv1)-(derv2)): diagonalise B = D^T D = V diag(beta) V^T,
+ * form alpha, gamma, zeta = diag(V^T {C, Gamma, Z} V), find the exact step t
+ * by Brent on phi'(t), then M = S^{-1/2} with
+ * S = XX + t (XD + XD^T) + t^2 B, the measured Gram of X + tD.
+ * Inputs (device, p x p): C = X^T Y, B = D^T D, Gam = D^T W, Z = D^T R,
+ * XX = X^T X, XD = X^T D. Outputs (device): M (p x p) and
+ * out[0..3] = {t, phi(t) model value, brent evaluations, status}.
+ * status 0 = ok, 5 = S not positive definite. */
+gsi_status gsi_linesearch(int32_t p, const double* C, const double* B, const double* Gam,
+                          const double* Z, const double* XX, const double* XD, double* M,
+                          double* out, void* stream);
+
+/* Retraction with the AX recursion (Eqs. (Ynew), (save_matvec)):
+ * X <- (X + t D) M, Y <- (Y + t W) M, in place. */
+gsi_status gsi_retract(int64_t n, int32_t p, double t, const double* M, double* X,
+                       const double* D, double* Y, const double* W, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSI_H */

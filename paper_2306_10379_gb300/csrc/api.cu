@@ -1,0 +1,96 @@
+// Kernel-level C entry points: the steps of one iteration, exposed for
+// parity tests and benchmarks. Temporary buffers are stream-ordered
+// allocations on the caller's stream.
+#include <algorithm>
+
+#include "blas_f64.cuh"
+
+using namespace gsi;
+
+namespace {
+
+struct ScratchGuard {
+  void* ptr = nullptr;
+  cudaStream_t st;
+  explicit ScratchGuard(cudaStream_t s) : st(s) {}
+  ~ScratchGuard() {
+    if (ptr) cudaFreeAsync(ptr, st);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+gsi_status gsi_spmm_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                        const double* val, int32_t p, const double* X, double* W,
+                        void* stream) {
+  if (n < 0 || p < 1 || (n > 0 && (!rowptr || !colidx || !val || !X || !W))) return GSI_ERR_ARG;
+  return spmm_csr(n, rowptr, colidx, val, p, X, W, (cudaStream_t)stream);
+}
+
+gsi_status gsi_spmm_sell(int64_t n, int64_t nchunks, int32_t C, const int64_t* perm,
+                         const int64_t* chunk_ptr, const int64_t* chunk_len,
+                         const int32_t* sell_col, const double* sell_val, int32_t p,
+                         const double* X, double* W, void* stream) {
+  if (n < 0 || nchunks < 0 || C <= 0 || p < 1 || nchunks * C < n) return GSI_ERR_ARG;
+  if (nchunks > 0 && (!perm || !chunk_ptr || !chunk_len || !sell_col || !sell_val || !X || !W))
+    return GSI_ERR_ARG;
+  return spmm_sell(n, nchunks, C, perm, chunk_ptr, chunk_len, sell_col, sell_val, p, X, W,
+                   (cudaStream_t)stream);
+}
+
+gsi_status gsi_gram(int64_t n, int32_t p, int32_t q, const double* U, const double* V,
+                    double* G, void* stream) {
+  if (n < 0 || p < 1 || q < 1 || p > 128 || q > 128 || !G || (n > 0 && (!U || !V)))
+    return GSI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ScratchGuard g(st);
+  size_t bytes = std::max<size_t>(gram_scratch_doubles(n, p, q), 1) * sizeof(double);
+  GSI_CUDA_TRY(cudaMallocAsync(&g.ptr, bytes, st));
+  return gram(n, p, q, U, V, G, (double*)g.ptr, st);
+}
+
+gsi_status gsi_residual(int64_t n, int32_t p, const double* X, const double* Y,
+                        const double* C, double* R, void* stream) {
+  if (n < 0 || p < 1 || p > 128 || (n > 0 && (!X || !Y || !C || !R))) return GSI_ERR_ARG;
+  RowMulArgs a{};
+  a.nk = 1;
+  a.U[0] = X;
+  a.M[0] = C;
+  a.s[0] = -1.0;
+  a.ne = 1;
+  a.E[0] = Y;
+  a.c[0] = 1.0;
+  return rowmul(n, p, a, R, (cudaStream_t)stream);
+}
+
+gsi_status gsi_linesearch(int32_t p, const double* C, const double* B, const double* Gam,
+                          const double* Z, const double* XX, const double* XD, double* M,
+                          double* out, void* stream) {
+  if (p < 1 || p > 128 || !C || !B || !Gam || !Z || !XX || !XD || !M || !out) return GSI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ScratchGuard g(st);
+  GSI_CUDA_TRY(cudaMallocAsync(&g.ptr, small_scratch_doubles(p) * sizeof(double), st));
+  return small_step(0, p, C, B, Gam, Z, XX, XD, M, out, (double*)g.ptr, st);
+}
+
+gsi_status gsi_retract(int64_t n, int32_t p, double t, const double* M, double* X,
+                       const double* D, double* Y, const double* W, void* stream) {
+  if (n < 0 || p < 1 || p > 128 || !M || (n > 0 && (!X || !D || !Y || !W))) return GSI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  RowMulArgs a{};
+  a.nk = 2;
+  a.U[0] = X;
+  a.M[0] = M;
+  a.s[0] = 1.0;
+  a.U[1] = D;
+  a.M[1] = M;
+  a.s[1] = t;
+  GSI_TRY(rowmul(n, p, a, X, st));
+  a.U[0] = Y;
+  a.U[1] = W;
+  return rowmul(n, p, a, Y, st);
+}
+
+}  // extern "C"

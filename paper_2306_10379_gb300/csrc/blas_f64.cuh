@@ -1,0 +1,42 @@
+// Internal interface of the float64 block kernels (see blas_f64.cu).
+#pragma once
+#include "common.cuh"
+
+namespace gsi {
+
+struct RowMulArgs {
+  int nk;               // number of right-multiplied terms (0..2)
+  const double* U[2];   // n x p blocks
+  const double* M[2];   // p x p matrices (device)
+  double s[2];          // scalars of the product terms
+  int ne;               // number of elementwise terms (0..2)
+  const double* E[2];   // n x p blocks
+  double c[2];          // scalars of the elementwise terms
+};
+
+gsi_status spmm_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* val,
+                    int p, const double* X, double* W, cudaStream_t st);
+gsi_status spmm_sell(int64_t n, int64_t nchunks, int C, const int64_t* perm,
+                     const int64_t* chunk_ptr, const int64_t* chunk_len, const int32_t* scol,
+                     const double* sval, int p, const double* X, double* W, cudaStream_t st);
+size_t gram_scratch_doubles(int64_t n, int p, int q);
+gsi_status gram(int64_t n, int p, int q, const double* U, const double* V, double* G,
+                double* scratch, cudaStream_t st);
+gsi_status rowmul(int64_t n, int p, const RowMulArgs& a, double* out, cudaStream_t st);
+int dots_blocks(int64_t n);
+gsi_status dots(int64_t n, int p, int ndots, const double* A0, const double* B0,
+                const double* A1, const double* B1, const double* Rnorm, double* out,
+                double* scratch, cudaStream_t st);
+
+// p x p step (small.cu)
+size_t small_scratch_doubles(int p);
+// mode 0: line search + polar factor (see gsi_linesearch); mode 1: M = S^{-1/2}
+// of the symmetric positive definite S given in `B` (start-block orthonormalisation).
+gsi_status small_step(int mode, int p, const double* C, const double* B, const double* Gam,
+                      const double* Z, const double* XX, const double* XD, double* M,
+                      double* out, double* scratch, cudaStream_t st);
+// theta (descending) and U with C = U diag(theta) U^T, C symmetrised first.
+gsi_status small_eig(int p, const double* C, double* theta, double* U, double* scratch,
+                     cudaStream_t st);
+
+}  // namespace gsi

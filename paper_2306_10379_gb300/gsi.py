@@ -1,0 +1,318 @@
+"""Python binding of libgsi.so (ctypes). Argument marshalling only: every step
+of the method runs in the library's CUDA kernels. PyTorch supplies device
+memory and the current stream.
+
+If libgsi.so has not been built this module raises on first use; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgsi.so")
+
+GSI_OK, GSI_ERR_ARG, GSI_ERR_CUDA, GSI_ERR_OOM, GSI_ERR_NOCONV, GSI_ERR_BREAKDOWN, \
+    GSI_ERR_NONFINITE, GSI_ERR_TIMEOUT = range(8)
+GSI_CSR, GSI_SELL = 0, 1
+GSI_SD, GSI_CG = 0, 1
+
+EXPORTED = [
+    "gsi_default_opts", "gsi_create", "gsi_step", "gsi_solve", "gsi_get_basis", "gsi_state_ptrs",
+    "gsi_destroy", "gsi_status_str", "gsi_last_error", "gsi_spmm_csr", "gsi_sell_size",
+    "gsi_csr_to_sell", "gsi_spmm_sell", "gsi_gram", "gsi_residual", "gsi_linesearch",
+    "gsi_retract",
+]
+
+
+class GsiError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib().gsi_status_str(status).decode()
+        extra = _lib().gsi_last_error().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({extra})" if extra and status == GSI_ERR_CUDA else ""))
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("fmt", ctypes.c_int32), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("sell_C", ctypes.c_int32), ("sell_sigma", ctypes.c_int32),
+                ("on_device", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("which", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("anorm", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("k_restart", ctypes.c_int32), ("recompute_every", ctypes.c_int32),
+                ("explicit_ax", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("matvecs", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("brent_evals", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("rel_residual_inf", ctypes.c_double), ("trace", ctypes.c_double),
+                ("last_step", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2306_10379_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "gsi_default_opts": [ctypes.POINTER(Opts)],
+            "gsi_create": [ctypes.POINTER(Matrix), i32, vp, i32, ctypes.POINTER(Opts), vp,
+                           ctypes.POINTER(vp)],
+            "gsi_step": [vp, i32, ctypes.POINTER(Info)],
+            "gsi_solve": [vp, ctypes.POINTER(Info)],
+            "gsi_get_basis": [vp, vp, vp, i32],
+            "gsi_state_ptrs": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)],
+            "gsi_destroy": [vp],
+            "gsi_spmm_csr": [i64, vp, vp, vp, i32, vp, vp, vp],
+            "gsi_sell_size": [i64, vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+            "gsi_csr_to_sell": [i64, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp],
+            "gsi_spmm_sell": [i64, i64, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp],
+            "gsi_gram": [i64, i32, i32, vp, vp, vp, vp],
+            "gsi_residual": [i64, i32, vp, vp, vp, vp, vp],
+            "gsi_linesearch": [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "gsi_retract": [i64, i32, dbl, vp, vp, vp, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.gsi_status_str.argtypes = [ctypes.c_int]
+        L.gsi_status_str.restype = ctypes.c_char_p
+        L.gsi_last_error.argtypes = []
+        L.gsi_last_error.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def lib():
+    """The loaded ctypes library (raises if libgsi.so is missing)."""
+    return _lib()
+
+
+def _check(status, where):
+    if status != GSI_OK:
+        raise GsiError(status, where)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype=None, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory via __cuda_array_interface__."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+# ----------------------------------------------------------------------------
+# Kernel-level entry points (torch CUDA tensors in, results written in place)
+# ----------------------------------------------------------------------------
+
+def spmm_csr(rowptr, colidx, val, X, W, stream=None):
+    import torch
+    n, p = X.shape
+    _check(lib().gsi_spmm_csr(n, _dptr(rowptr, torch.int64), _dptr(colidx, torch.int32),
+                              _dptr(val, torch.float64), p, _dptr(X, torch.float64),
+                              _dptr(W, torch.float64, (n, p)), _stream(stream)), "gsi_spmm_csr")
+
+
+def csr_to_sell(n, rowptr, colidx, val, C=32, sigma=32):
+    """Host conversion (numpy arrays in, numpy arrays out)."""
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    colidx = np.ascontiguousarray(colidx, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    nch, tot = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().gsi_sell_size(n, rowptr.ctypes.data, C, sigma, ctypes.byref(nch), ctypes.byref(tot)),
+           "gsi_sell_size")
+    perm = np.empty(nch.value * C, np.int64)
+    cptr = np.empty(nch.value + 1, np.int64)
+    clen = np.empty(nch.value, np.int64)
+    scol = np.empty(tot.value, np.int32)
+    sval = np.empty(tot.value, np.float64)
+    _check(lib().gsi_csr_to_sell(n, rowptr.ctypes.data, colidx.ctypes.data, val.ctypes.data, C, sigma,
+                                 perm.ctypes.data, cptr.ctypes.data, clen.ctypes.data,
+                                 scol.ctypes.data, sval.ctypes.data), "gsi_csr_to_sell")
+    return perm, cptr, clen, scol, sval
+
+
+def spmm_sell(n, C, perm, chunk_ptr, chunk_len, scol, sval, X, W, stream=None):
+    import torch
+    p = X.shape[1]
+    nchunks = chunk_len.shape[0]
+    _check(lib().gsi_spmm_sell(n, nchunks, C, _dptr(perm, torch.int64), _dptr(chunk_ptr, torch.int64),
+                               _dptr(chunk_len, torch.int64), _dptr(scol, torch.int32),
+                               _dptr(sval, torch.float64), p, _dptr(X, torch.float64),
+                               _dptr(W, torch.float64, (n, p)), _stream(stream)), "gsi_spmm_sell")
+
+
+def gram(U, V, G, stream=None):
+    import torch
+    n, p = U.shape
+    q = V.shape[1]
+    _check(lib().gsi_gram(n, p, q, _dptr(U, torch.float64), _dptr(V, torch.float64, (n, q)),
+                          _dptr(G, torch.float64, (p, q)), _stream(stream)), "gsi_gram")
+
+
+def residual(X, Y, C, R, stream=None):
+    import torch
+    n, p = X.shape
+    _check(lib().gsi_residual(n, p, _dptr(X, torch.float64), _dptr(Y, torch.float64, (n, p)),
+                              _dptr(C, torch.float64, (p, p)), _dptr(R, torch.float64, (n, p)),
+                              _stream(stream)), "gsi_residual")
+
+
+def linesearch(C, B, Gam, Z, XX, XD, M, out, stream=None):
+    import torch
+    p = C.shape[0]
+    f = torch.float64
+    _check(lib().gsi_linesearch(p, _dptr(C, f, (p, p)), _dptr(B, f, (p, p)), _dptr(Gam, f, (p, p)),
+                                _dptr(Z, f, (p, p)), _dptr(XX, f, (p, p)), _dptr(XD, f, (p, p)),
+                                _dptr(M, f, (p, p)), _dptr(out, f), _stream(stream)), "gsi_linesearch")
+
+
+def retract(t, M, X, D, Y, W, stream=None):
+    import torch
+    n, p = X.shape
+    f = torch.float64
+    _check(lib().gsi_retract(n, p, float(t), _dptr(M, f, (p, p)), _dptr(X, f), _dptr(D, f, (n, p)),
+                             _dptr(Y, f, (n, p)), _dptr(W, f, (n, p)), _stream(stream)), "gsi_retract")
+
+
+# ----------------------------------------------------------------------------
+# Solver context
+# ----------------------------------------------------------------------------
+
+class Solver:
+    """gsi_create / gsi_step / gsi_solve / gsi_get_basis / gsi_destroy.
+
+    A: object with n, rowptr, colidx, val (numpy host arrays or torch CUDA
+    tensors). X0: n x p start block (numpy or torch CUDA float64)."""
+
+    def __init__(self, A, p, X0, method="sd", which=1, tol=1e-8, anorm=0.0, max_iters=10000,
+                 k_restart=0, recompute_every=50, explicit_ax=False, fmt="csr", stream=None):
+        import torch
+        L = lib()
+        self._keep = []
+        on_dev = isinstance(A.rowptr, torch.Tensor)
+        if on_dev:
+            rp, ci, va = _dptr(A.rowptr, torch.int64), _dptr(A.colidx, torch.int32), _dptr(A.val, torch.float64)
+            nnz = int(A.colidx.numel())
+        else:
+            arrs = [np.ascontiguousarray(A.rowptr, np.int64), np.ascontiguousarray(A.colidx, np.int32),
+                    np.ascontiguousarray(A.val, np.float64)]
+            self._keep += arrs
+            rp, ci, va = (ctypes.c_void_p(a.ctypes.data) for a in arrs)
+            nnz = int(arrs[1].size)
+        m = Matrix(GSI_SELL if fmt == "sell" else GSI_CSR, int(A.n), nnz, rp, ci, va, 32, 32, 1 if on_dev else 0)
+        o = Opts()
+        L.gsi_default_opts(ctypes.byref(o))
+        o.method = GSI_CG if method == "cg" else GSI_SD
+        o.which = int(which)
+        o.tol = float(tol)
+        o.anorm = float(anorm)
+        o.max_iters = int(max_iters)
+        o.k_restart = int(k_restart)
+        o.recompute_every = int(recompute_every)
+        o.explicit_ax = 1 if explicit_ax else 0
+        if isinstance(X0, torch.Tensor):
+            x0p, x0dev = _dptr(X0, torch.float64, (A.n, p)), 1
+        else:
+            X0 = np.ascontiguousarray(X0, np.float64)
+            self._keep.append(X0)
+            x0p, x0dev = ctypes.c_void_p(X0.ctypes.data), 0
+        self.n, self.p = int(A.n), int(p)
+        self._stream = stream
+        ctx = ctypes.c_void_p()
+        _check(L.gsi_create(ctypes.byref(m), int(p), x0p, x0dev, ctypes.byref(o), _stream(stream),
+                            ctypes.byref(ctx)), "gsi_create")
+        self._ctx = ctx
+        self._keep = []
+
+    def step(self, nsteps=1):
+        info = Info()
+        _check(lib().gsi_step(self._ctx, int(nsteps), ctypes.byref(info)), "gsi_step")
+        return info.as_dict()
+
+    def solve(self, raise_on_noconv=False):
+        info = Info()
+        s = lib().gsi_solve(self._ctx, ctypes.byref(info))
+        if s != GSI_OK and (s != GSI_ERR_NOCONV or raise_on_noconv):
+            raise GsiError(s, "gsi_solve")
+        return info.as_dict()
+
+    def basis(self, evals=True, device=False):
+        """(X, evals): Ritz vectors and values (evals=True), or the raw iterate."""
+        import torch
+        if device:
+            X = torch.empty((self.n, self.p), dtype=torch.float64, device="cuda")
+            ev = torch.empty(self.p, dtype=torch.float64, device="cuda") if evals else None
+            _check(lib().gsi_get_basis(self._ctx, ctypes.c_void_p(X.data_ptr()),
+                                       ctypes.c_void_p(ev.data_ptr()) if evals else None, 1),
+                   "gsi_get_basis")
+            return X, ev
+        X = np.empty((self.n, self.p))
+        ev = np.empty(self.p) if evals else None
+        _check(lib().gsi_get_basis(self._ctx, ctypes.c_void_p(X.ctypes.data),
+                                   ctypes.c_void_p(ev.ctypes.data) if evals else None, 0),
+               "gsi_get_basis")
+        return X, ev
+
+    def state(self):
+        """Zero-copy torch views of the current X and Y = AX (library memory)."""
+        import torch
+        xp, yp = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().gsi_state_ptrs(self._ctx, ctypes.byref(xp), ctypes.byref(yp)), "gsi_state_ptrs")
+        X = torch.as_tensor(_DeviceArray(xp.value, (self.n, self.p)), device="cuda")
+        Y = torch.as_tensor(_DeviceArray(yp.value, (self.n, self.p)), device="cuda")
+        return X, Y
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().gsi_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
