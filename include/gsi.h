@@ -195,6 +195,39 @@ gsi_status gsi_linesearch(int32_t p, const double* C, const double* B, const dou
 gsi_status gsi_retract(int64_t n, int32_t p, double t, const double* M, double* X,
                        const double* D, double* Y, const double* W, void* stream);
 
+/* ------------------------------------------------------------------------
+ * df64 kernels. A df64 array holds each value as two float32 (hi, lo),
+ * interleaved (value i at [2i], [2i+1]), hi + lo exact, |lo| <= ulp(hi)/2:
+ * a 48-bit significand. The solver stores every n x p block this way and
+ * computes its block products with float64-accurate (error-free split)
+ * products on the BF16 tensor cores.
+ * ---------------------------------------------------------------------- */
+
+/* W = A X in df64 (Sec. 6.1, one block matvec): CSR A with df64 values
+ * (val: 2*nnz floats), X and W n x p df64. */
+gsi_status gsi_df_spmm_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                           const float* val, int32_t p, const float* X, float* W, void* stream);
+
+/* OUT = s0 U0 M0 (+ s1 U1 M1 if nk = 2) (+ c0 E0) (+ c1 E1): n x p df64 blocks
+ * U*, E*, OUT; M* float64 p x p; c* df64 scalars given as (hi, lo) float
+ * pairs (c: 4 floats, c0 then c1). ne = number of E terms (0..2). The
+ * products are exact up to the 49-bit digit truncation of the operands
+ * (relative error about 2^-45 of sum |U||M|), i.e. float64-class; this is
+ * the right multiplication of Eqs. (gradPhi) (R = Y - XC), (Pnew) and
+ * (Ynew)/(save_matvec). OUT may alias an E; it may alias a U only if p <= 64.
+ * Uses temporary device memory (stream-ordered allocation). */
+gsi_status gsi_oz_gemm(int64_t n, int32_t p, int32_t nk, const float* U0, const float* U1,
+                       const double* M0, const double* M1, double s0, double s1, int32_t ne,
+                       const float* E0, const float* E1, const float* c, float* OUT,
+                       void* stream);
+
+/* G = U^T V (float64 p x q) from n x p and n x q df64 blocks, float64-class
+ * accurate (the Gram products of Eqs. (gradPhi), (diags), (CG_linesearch_D)).
+ * sym = 1 requires U == V and computes only the upper half. Uses temporary
+ * device memory (stream-ordered allocation). */
+gsi_status gsi_oz_gram(int64_t n, int32_t p, int32_t q, const float* U, const float* V,
+                       int32_t sym, double* G, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

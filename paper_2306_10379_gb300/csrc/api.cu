@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "blas_f64.cuh"
+#include "oz.cuh"
 
 using namespace gsi;
 
@@ -91,6 +92,47 @@ gsi_status gsi_retract(int64_t n, int32_t p, double t, const double* M, double* 
   a.U[0] = Y;
   a.U[1] = W;
   return rowmul(n, p, a, Y, st);
+}
+
+gsi_status gsi_df_spmm_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                           const float* val, int32_t p, const float* X, float* W, void* stream) {
+  if (n < 0 || p < 1 || (n > 0 && (!rowptr || !colidx || !val || !X || !W))) return GSI_ERR_ARG;
+  return df_spmm_csr(n, rowptr, colidx, reinterpret_cast<const float2*>(val), p,
+                     reinterpret_cast<const float2*>(X), reinterpret_cast<float2*>(W),
+                     (cudaStream_t)stream);
+}
+
+gsi_status gsi_oz_gemm(int64_t n, int32_t p, int32_t nk, const float* U0, const float* U1,
+                       const double* M0, const double* M1, double s0, double s1, int32_t ne,
+                       const float* E0, const float* E1, const float* c, float* OUT,
+                       void* stream) {
+  if (n < 0 || p < 1 || p > 128 || nk < 1 || nk > 2 || ne < 0 || ne > 2 || !U0 || !M0 || !OUT ||
+      (nk == 2 && (!U1 || !M1)) || (ne > 0 && (!c || !E0)) || (ne > 1 && !E1))
+    return GSI_ERR_ARG;
+  if (n == 0) return GSI_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  ScratchGuard g(st);
+  GSI_CUDA_TRY(cudaMallocAsync(&g.ptr, oz_rhs_bytes(p, nk), st));
+  const float2* U[2] = {reinterpret_cast<const float2*>(U0), reinterpret_cast<const float2*>(U1)};
+  const double* M[2] = {M0, M1};
+  double s[2] = {s0, s1};
+  const float2* E[2] = {reinterpret_cast<const float2*>(E0), reinterpret_cast<const float2*>(E1)};
+  float2 ce[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  for (int m = 0; m < ne; ++m) ce[m] = make_float2(c[2 * m], c[2 * m + 1]);
+  return oz_gemm(n, p, nk, U, M, s, ne, E, ce, reinterpret_cast<float2*>(OUT), nullptr, nullptr,
+                 false, g.ptr, st, nullptr);
+}
+
+gsi_status gsi_oz_gram(int64_t n, int32_t p, int32_t q, const float* U, const float* V,
+                       int32_t sym, double* G, void* stream) {
+  if (n < 0 || p < 1 || q < 1 || p > 128 || q > 128 || !G || (n > 0 && (!U || !V)) ||
+      (sym && (p != q || U != V)))
+    return GSI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ScratchGuard g(st);
+  GSI_CUDA_TRY(cudaMallocAsync(&g.ptr, std::max<size_t>(oz_gram_scratch_bytes(n, p, q, sym != 0), 16), st));
+  return oz_gram(n, p, q, reinterpret_cast<const float2*>(U), reinterpret_cast<const float2*>(V),
+                 sym != 0, G, reinterpret_cast<float2*>(g.ptr), st);
 }
 
 }  // extern "C"

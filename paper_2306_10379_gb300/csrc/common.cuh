@@ -18,6 +18,9 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // Number of SMs of the current device (cached per process).
 int sm_count();
 
+// Count of kernels launched by this library in this process.
+void note_launch();
+
 }  // namespace gsi
 
 #define GSI_CUDA_TRY(expr)                                         \
@@ -26,7 +29,11 @@ int sm_count();
     if (_e != cudaSuccess) return gsi::cuda_status(_e);            \
   } while (0)
 
-#define GSI_LAUNCH_CHECK() GSI_CUDA_TRY(cudaGetLastError())
+#define GSI_LAUNCH_CHECK()  \
+  do {                      \
+    gsi::note_launch();     \
+    GSI_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
 
 #define GSI_TRY(expr)                                              \
   do {                                                             \

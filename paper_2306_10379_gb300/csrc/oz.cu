@@ -1,0 +1,622 @@
+// Float64-accurate block products on the BF16 tensor cores (error-free
+// splitting after Ozaki, Ogita, Oishi & Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59, 2012), for the two contraction
+// shapes of one iteration:
+//   oz_gemm : OUT = sum_k U_k M_k + sum_e c_e E_e   (n x p blocks times p x p)
+//   oz_gram : G   = U^T V                          (contraction over the n rows)
+// Block data is df64 (float2 = hi, lo). Every operand is cut into ND = 7
+// signed "digits" d_i in [-128, 128] on a fixed-point grid set by a power of
+// two per row (gemm, left operand), per column (p x p right operand) or per
+// column and 64-row chunk (gram):
+//   x = 2^(E-7) * sum_{i<7} d_i 2^(-7 i)   (truncation below 2^(E-49)).
+// Digits are exact in bf16, products of two digits are exact in fp32, and the
+// 28 digit pairs (i + i' <= 6) are summed per "group" g = i + i' in fp32
+// accumulators whose partial sums stay below 2^24 for contraction lengths up
+// to 256, so the tensor-core accumulation is exact. The 7 group sums are then
+// combined in df64: OUT = 2^(E_r + F_j - 14) sum_g S_g 2^(-7 g).
+#include <cuda_bf16.h>
+
+#include "df.cuh"
+#include "oz.cuh"
+
+namespace gsi {
+
+constexpr int ND = 7;
+constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23: x + MAGIC - MAGIC rounds x to an integer
+
+__device__ __forceinline__ int exponent_above(float maxabs) {
+  // smallest E with maxabs < 2^E, clamped to keep 2^(7-E) finite in fp32
+  if (!(maxabs > 0.0f)) return 0;
+  int e = ((__float_as_int(maxabs) >> 23) & 255) - 127;
+  return max(e + 1, -100);
+}
+
+// The 7 digits of (h + l) on the grid of 2^(E-7): digits 0..2 come from h
+// alone, then l is folded in (at that point h's remainder is a multiple of
+// 2^4 in the digit frame and |l| <= 8, so one rounding of at most 2^-45 of
+// the scale can occur), digits 3..6 follow. Each step is exact:
+// d = rint(a), a <- 128 (a - d).
+__device__ __forceinline__ void digits7(float h, float l, int E, float d[ND]) {
+  const float s = exp2i(7 - E);
+  float a = __fmul_rn(h, s);
+  float b = __fmul_rn(__fmul_rn(l, s), 2097152.0f);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    if (i == 3) a = __fadd_rn(a, b);
+    float t = __fadd_rn(a, MAGIC);
+    float di = __fsub_rn(t, MAGIC);
+    d[i] = di;
+    a = __fmul_rn(__fsub_rn(a, di), 128.0f);
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// sum_g S_g 2^(-7 g) as df64 (Horner from the smallest group, TwoSum per step)
+__device__ __forceinline__ float2 combine_groups(const float S[ND]) {
+  float h = S[ND - 1], l = 0.0f;
+#pragma unroll
+  for (int g = ND - 2; g >= 0; --g) {
+    float hs = __fmul_rn(h, 0.0078125f);
+    l = __fmul_rn(l, 0.0078125f);
+    float2 t = two_sum(S[g], hs);
+    h = t.x;
+    l = __fadd_rn(l, t.y);
+  }
+  return fast_two_sum(h, l);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t r[2], const void* p) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t r[2], const void* p) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(a));
+}
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ---------------------------------------------------------------------------
+// Right operand: B = [s_0 M_0; s_1 M_1] (K = nk*p rows, p columns, float64),
+// cut into digits with one power of two per column. Layout for the tensor
+// cores: Md[plane][n][k] (k contiguous, K16 = K rounded up to 16), F[n].
+// One block per column n.
+// ---------------------------------------------------------------------------
+__global__ void oz_prep_rhs_kernel(int p, int p16, int nk, int K16, const double* M0,
+                                   const double* M1, double s0, double s1,
+                                   __nv_bfloat16* Md, int* F) {
+  const int n = blockIdx.x;
+  __shared__ float red[32];
+  __shared__ int sE;
+  const int K = nk * p;
+  float mx = 0.0f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    int kk = k / p, l = k - kk * p;
+    double v = (n < p) ? (kk == 0 ? s0 * M0[l * p + n] : s1 * M1[l * p + n]) : 0.0;
+    mx = fmaxf(mx, fabsf((float)v));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    sE = exponent_above(m);
+    F[n] = sE;
+  }
+  __syncthreads();
+  const int E = sE;
+  for (int k = threadIdx.x; k < K16; k += blockDim.x) {
+    double v = 0.0;
+    if (k < K && n < p) {
+      int kk = k / p, l = k - kk * p;
+      v = (kk == 0 ? s0 * M0[l * p + n] : s1 * M1[l * p + n]);
+    }
+    float2 x = df_from_double(v);
+    float d[ND];
+    digits7(x.x, x.y, E, d);
+#pragma unroll
+    for (int i = 0; i < ND; ++i)
+      Md[((size_t)i * p16 + n) * K16 + k] = __float2bfloat16_rn(d[i]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// oz_gemm: rows in tiles of RT = 32, output columns in slices of up to 64
+// (blockIdx.y). 8 warps: 2 row groups of 16 x 4 column groups; each warp owns
+// up to 2 n-tiles of 8 columns.
+// ---------------------------------------------------------------------------
+constexpr int GM_RT = 32;
+constexpr int GM_THREADS = 256;
+
+__host__ __device__ inline int gm_ud_stride(int K16) { return K16 + 8; }   // bf16 elements per row
+__host__ __device__ inline int gm_md_stride(int K16) { return K16 + 8; }
+
+size_t oz_gemm_smem(int K16, int NC) {
+  return (size_t)ND * GM_RT * gm_ud_stride(K16) * 2 + (size_t)ND * NC * gm_md_stride(K16) * 2 +
+         (GM_RT + NC) * sizeof(int);
+}
+
+__global__ void __launch_bounds__(GM_THREADS)
+oz_gemm_kernel(int64_t n, int p, int p16, int nk, int K16, OzGemmArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int col0 = blockIdx.y * 64;
+  const int NC = min(64, p16 - col0);
+  const int uds = gm_ud_stride(K16), mds = gm_md_stride(K16);
+  __nv_bfloat16* Ud = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* Ms = Ud + (size_t)ND * GM_RT * uds;
+  int* Er = reinterpret_cast<int*>(Ms + (size_t)ND * NC * mds);
+  int* Fs = Er + GM_RT;
+  const int K = nk * p;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // right operand digits for this column slice
+  for (int e = tid; e < ND * NC * (K16 / 8); e += GM_THREADS) {
+    int chunk = e % (K16 / 8);
+    int rowi = e / (K16 / 8);
+    int plane = rowi / NC, nn = rowi - plane * NC;
+    const uint4* src = reinterpret_cast<const uint4*>(a.Md + ((size_t)plane * p16 + col0 + nn) * K16) + chunk;
+    *reinterpret_cast<uint4*>(Ms + ((size_t)plane * NC + nn) * mds + chunk * 8) = *src;
+  }
+  for (int e = tid; e < NC; e += GM_THREADS) Fs[e] = a.F[col0 + e];
+
+  float2 dacc0 = make_float2(0.f, 0.f), dacc1 = make_float2(0.f, 0.f);
+  const int64_t ntiles = (n + GM_RT - 1) / GM_RT;
+  const int wr = warp >> 2, wc = warp & 3;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * GM_RT;
+    __syncthreads();  // previous tile's readers are done with Ud / Er
+    // (a) row exponents over the K columns of [U_0 U_1]
+    for (int rr = warp; rr < GM_RT; rr += GM_THREADS / 32) {
+      int64_t R = r0 + rr;
+      float mx = 0.0f;
+      if (R < n) {
+        for (int k = lane; k < K; k += 32) {
+          int kk = k / p, l = k - kk * p;
+          mx = fmaxf(mx, fabsf(a.U[kk][R * p + l].x));
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) Er[rr] = exponent_above(mx);
+    }
+    __syncthreads();
+    // (b) digits of the row tile: one thread per (row, pair of columns)
+    for (int e = tid; e < GM_RT * (K16 / 2); e += GM_THREADS) {
+      int rr = e / (K16 / 2);
+      int k = 2 * (e - rr * (K16 / 2));
+      int64_t R = r0 + rr;
+      float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
+      if (R < n) {
+        if (k < K) {
+          int kk = k / p, l = k - kk * p;
+          x0 = a.U[kk][R * p + l];
+        }
+        if (k + 1 < K) {
+          int kk = (k + 1) / p, l = (k + 1) - kk * p;
+          x1 = a.U[kk][R * p + l];
+        }
+      }
+      int E = Er[rr];
+      float d0[ND], d1[ND];
+      digits7(x0.x, x0.y, E, d0);
+      digits7(x1.x, x1.y, E, d1);
+#pragma unroll
+      for (int i = 0; i < ND; ++i)
+        *reinterpret_cast<uint32_t*>(Ud + ((size_t)i * GM_RT + rr) * uds + k) = pack_bf16x2(d0[i], d1[i]);
+    }
+    __syncthreads();
+    // (c) tensor-core products, exact per digit-pair group
+    float acc[ND][2][4];
+#pragma unroll
+    for (int g = 0; g < ND; ++g)
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[g][t][q] = 0.0f;
+    const int ntl = NC / 8;
+    const bool act0 = wc < ntl, act1 = wc + 4 < ntl;
+    if (act0) {
+      for (int ks = 0; ks < K16 / 16; ++ks) {
+        uint32_t A[ND][4];
+        const int q = lane >> 3;
+#pragma unroll
+        for (int i = 0; i < ND; ++i)
+          ldsm_x4(A[i], Ud + ((size_t)i * GM_RT + wr * 16 + (lane & 7) + (q & 1) * 8) * uds +
+                            ks * 16 + (q >> 1) * 8);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (t == 1 && !act1) break;
+          const int nt = wc + 4 * t;
+#pragma unroll
+          for (int j = 0; j < ND; ++j) {
+            uint32_t B[2];
+            const int l16 = lane & 15;
+            ldsm_x2(B, Ms + ((size_t)j * NC + nt * 8 + (l16 & 7)) * mds + ks * 16 + (l16 >> 3) * 8);
+#pragma unroll
+            for (int i = 0; i < ND - j; ++i) mma_bf16(acc[i + j][t], A[i], B);
+          }
+        }
+      }
+    }
+    // (d) epilogue: df64 combination, scaling, elementwise terms, store
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (!(t == 0 ? act0 : act1)) continue;
+      const int nt = wc + 4 * t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rr = wr * 16 + (lane >> 2) + h * 8;
+        const int64_t R = r0 + rr;
+        const int cc = nt * 8 + (lane & 3) * 2;
+        if (R >= n) continue;
+        float2 v[2];
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          float S[ND];
+#pragma unroll
+          for (int g = 0; g < ND; ++g) S[g] = acc[g][t][h * 2 + e2];
+          float2 w = combine_groups(S);
+          int sc = Er[rr] + Fs[cc + e2] - 14;
+          if (sc >= -126) {
+            float f = exp2i(sc);
+            v[e2] = make_float2(w.x * f, w.y * f);
+          } else {
+            float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
+            v[e2] = make_float2(w.x * f1 * f2, w.y * f1 * f2);
+          }
+        }
+        const int C = col0 + cc;
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          if (C + e2 >= p) continue;
+          float2 y = v[e2];
+          const int64_t idx = R * p + C + e2;
+          for (int m = 0; m < a.ne; ++m) y = df_add(y, df_mul(a.ce[m], a.E[m][idx]));
+          if (a.dot_self) dacc0 = df_add(dacc0, df_mul(y, y));
+          if (a.dot_with) dacc1 = df_add(dacc1, df_mul(y, a.dot_with[idx]));
+          a.out[idx] = y;
+        }
+      }
+    }
+  }
+  if (a.dot_part) {
+    __shared__ float2 red[2][GM_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+      float2 t0 = make_float2(__shfl_xor_sync(0xffffffffu, dacc0.x, o), __shfl_xor_sync(0xffffffffu, dacc0.y, o));
+      float2 t1 = make_float2(__shfl_xor_sync(0xffffffffu, dacc1.x, o), __shfl_xor_sync(0xffffffffu, dacc1.y, o));
+      dacc0 = df_add(dacc0, t0);
+      dacc1 = df_add(dacc1, t1);
+    }
+    if (lane == 0) {
+      red[0][warp] = dacc0;
+      red[1][warp] = dacc1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+      for (int w = 0; w < GM_THREADS / 32; ++w) {
+        s0 = df_add(s0, red[0][w]);
+        s1 = df_add(s1, red[1][w]);
+      }
+      int b = blockIdx.y * gridDim.x + blockIdx.x;
+      a.dot_part[2 * b] = s0;
+      a.dot_part[2 * b + 1] = s1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// oz_gram: G = U^T V. Output in 64 x 64 blocks (blockIdx.y), rows in chunks of
+// GR_KC = 64 processed by the blocks of blockIdx.x in turn. 16 warps, each a
+// 16 x 16 output tile (2 n-tiles); per chunk the column exponents are taken
+// over the chunk's rows, so each chunk's digit products are exact, and the
+// chunk results are accumulated in df64 registers.
+// ---------------------------------------------------------------------------
+constexpr int GR_KC = 64;
+constexpr int GR_THREADS = 512;
+constexpr int GR_STRIDE = 64 + 8;
+
+size_t oz_gram_smem() { return (size_t)2 * ND * GR_KC * GR_STRIDE * 2 + 4 * 64 * sizeof(int); }
+
+__global__ void __launch_bounds__(GR_THREADS)
+oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
+               int sym, int nbj, float2* part) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* Ud = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* Vd = Ud + (size_t)ND * GR_KC * GR_STRIDE;
+  int* mxu = reinterpret_cast<int*>(Vd + (size_t)ND * GR_KC * GR_STRIDE);
+  int* mxv = mxu + 64;
+  int* Eu = mxv + 64;
+  int* Ev = Eu + 64;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // output block
+  int bi, bj;
+  {
+    int b = blockIdx.y;
+    if (sym) {  // upper-triangular enumeration
+      bi = 0;
+      while (b >= nbj - bi) {
+        b -= nbj - bi;
+        ++bi;
+      }
+      bj = bi + b;
+    } else {
+      bi = b / nbj;
+      bj = b - bi * nbj;
+    }
+  }
+  const int i0 = bi * 64, j0 = bj * 64;
+  const int wi = warp >> 2, wj = warp & 3;
+  const bool active = (i0 + wi * 16 < p) && (j0 + wj * 16 < q) && !(sym && bi == bj && wi > wj);
+  float2 res[2][4];
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) res[t][e] = make_float2(0.f, 0.f);
+  const int64_t nchunks = (n + GR_KC - 1) / GR_KC;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t r0 = ch * GR_KC;
+    __syncthreads();
+    if (tid < 128) mxu[tid] = 0;  // mxu and mxv are adjacent
+    __syncthreads();
+    // (a) column maxima of |hi| over the chunk
+    for (int e = tid; e < GR_KC * 64; e += GR_THREADS) {
+      int r = e >> 6, c = e & 63;
+      int64_t R = r0 + r;
+      if (R < n) {
+        if (i0 + c < p) atomicMax(&mxu[c], __float_as_int(fabsf(U[R * p + i0 + c].x)));
+        if (j0 + c < q) atomicMax(&mxv[c], __float_as_int(fabsf(V[R * q + j0 + c].x)));
+      }
+    }
+    __syncthreads();
+    if (tid < 64) Eu[tid] = exponent_above(__int_as_float(mxu[tid]));
+    else if (tid < 128) Ev[tid - 64] = exponent_above(__int_as_float(mxv[tid - 64]));
+    __syncthreads();
+    // (b) digits: one thread per (row, pair of columns), U then V
+    for (int e = tid; e < 2 * GR_KC * 32; e += GR_THREADS) {
+      const bool isv = e >= GR_KC * 32;
+      int e2 = isv ? e - GR_KC * 32 : e;
+      int r = e2 >> 5, c = 2 * (e2 & 31);
+      int64_t R = r0 + r;
+      const float2* src = isv ? V : U;
+      const int ld = isv ? q : p, c0 = isv ? j0 : i0;
+      float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
+      if (R < n) {
+        if (c0 + c < ld) x0 = src[R * ld + c0 + c];
+        if (c0 + c + 1 < ld) x1 = src[R * ld + c0 + c + 1];
+      }
+      const int* Ex = isv ? Ev : Eu;
+      float d0[ND], d1[ND];
+      digits7(x0.x, x0.y, Ex[c], d0);
+      digits7(x1.x, x1.y, Ex[c + 1], d1);
+      __nv_bfloat16* dst = isv ? Vd : Ud;
+#pragma unroll
+      for (int i = 0; i < ND; ++i)
+        *reinterpret_cast<uint32_t*>(dst + ((size_t)i * GR_KC + r) * GR_STRIDE + c) = pack_bf16x2(d0[i], d1[i]);
+    }
+    __syncthreads();
+    if (active) {
+      float acc[ND][2][4];
+#pragma unroll
+      for (int g = 0; g < ND; ++g)
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[g][t][e] = 0.0f;
+#pragma unroll
+      for (int ks = 0; ks < GR_KC / 16; ++ks) {
+        uint32_t A[ND][4];
+        const int qq = lane >> 3;
+#pragma unroll
+        for (int i = 0; i < ND; ++i)
+          ldsm_x4_t(A[i], Ud + ((size_t)i * GR_KC + ks * 16 + (lane & 7) + (qq >> 1) * 8) * GR_STRIDE +
+                              wi * 16 + (qq & 1) * 8);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+#pragma unroll
+          for (int j = 0; j < ND; ++j) {
+            uint32_t B[2];
+            const int l16 = lane & 15;
+            ldsm_x2_t(B, Vd + ((size_t)j * GR_KC + ks * 16 + (l16 & 7) + (l16 >> 3) * 8) * GR_STRIDE +
+                             wj * 16 + t * 8);
+#pragma unroll
+            for (int i = 0; i < ND - j; ++i) mma_bf16(acc[i + j][t], A[i], B);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int ii = wi * 16 + (lane >> 2) + (e >> 1) * 8;
+          const int jj = wj * 16 + t * 8 + (lane & 3) * 2 + (e & 1);
+          float S[ND];
+#pragma unroll
+          for (int g = 0; g < ND; ++g) S[g] = acc[g][t][e];
+          float2 w = combine_groups(S);
+          int sc = Eu[ii] + Ev[jj] - 14;
+          float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
+          res[t][e] = df_add(res[t][e], make_float2(w.x * f1 * f2, w.y * f1 * f2));
+        }
+    }
+  }
+  if (active) {
+    float2* out = part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * 64 * 64;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int ii = wi * 16 + (lane >> 2) + (e >> 1) * 8;
+        const int jj = wj * 16 + t * 8 + (lane & 3) * 2 + (e & 1);
+        out[ii * 64 + jj] = res[t][e];
+      }
+  }
+}
+
+// Fixed-order sum of the per-block partials into G (float64, p x q); the
+// symmetric case fills the lower triangle from the upper one.
+__global__ void oz_gram_reduce_kernel(int p, int q, int nsplit, int nblk, int sym, int nbj,
+                                      const float2* part, double* G) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p * q) return;
+  int i = e / q, j = e - i * q;
+  int si = i, sj = j;
+  if (sym && i > j) {
+    si = j;
+    sj = i;
+  }
+  int bi = si / 64, bj = sj / 64;
+  int b;
+  if (sym) {
+    b = 0;
+    for (int r = 0; r < bi; ++r) b += nbj - r;
+    b += bj - bi;
+  } else {
+    b = bi * nbj + bj;
+  }
+  int ii = si - bi * 64, jj = sj - bj * 64;
+  if (sym && bi == bj && (ii / 16) > (jj / 16)) {  // lower warp tile inside a diagonal block
+    int t = ii;
+    ii = jj;
+    jj = t;
+  }
+  float2 s = make_float2(0.f, 0.f);
+  for (int k = 0; k < nsplit; ++k) s = df_add(s, part[((size_t)k * nblk + b) * 4096 + ii * 64 + jj]);
+  G[e] = df_to_double(s);
+}
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+int pad16(int x) { return (x + 15) / 16 * 16; }
+
+size_t oz_rhs_bytes(int p, int nk) {
+  return (size_t)ND * pad16(p) * pad16(nk * p) * sizeof(__nv_bfloat16) + pad16(p) * sizeof(int) + 256;
+}
+
+gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const double* const M[2],
+                   const double s[2], int ne, const float2* const E[2], const float2 ce[2],
+                   float2* out, float2* dot_part, const float2* dot_with, bool dot_self,
+                   void* rhs_ws, cudaStream_t st, int* nparts) {
+  if (nk < 1 || nk > 2 || ne < 0 || ne > 2 || nk * p > 256) return GSI_ERR_ARG;
+  if (nk == 2 && pad16(2 * p) > 128) {
+    // shared memory holds K <= 128: OUT = U_0 M_0 + E terms, then OUT += U_1 M_1
+    if (pad16(p) > 64 && (U[0] == out || U[1] == out)) return GSI_ERR_ARG;
+    const float2* U0[2] = {U[0], U[0]};
+    const double* M0[2] = {M[0], M[0]};
+    double s0[2] = {s[0], 0.0};
+    GSI_TRY(oz_gemm(n, p, 1, U0, M0, s0, ne, E, ce, out, nullptr, nullptr, false, rhs_ws, st,
+                    nullptr));
+    const float2* U1[2] = {U[1], U[1]};
+    const double* M1[2] = {M[1], M[1]};
+    double s1[2] = {s[1], 0.0};
+    const float2* E1[2] = {out, out};
+    float2 c1[2] = {make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
+    return oz_gemm(n, p, 1, U1, M1, s1, 1, E1, c1, out, dot_part, dot_with, dot_self, rhs_ws, st,
+                   nparts);
+  }
+  const int p16 = pad16(p), K16 = pad16(nk * p);
+  __nv_bfloat16* Md = reinterpret_cast<__nv_bfloat16*>(rhs_ws);
+  int* F = reinterpret_cast<int*>(reinterpret_cast<char*>(rhs_ws) +
+                                  (size_t)ND * p16 * K16 * sizeof(__nv_bfloat16));
+  oz_prep_rhs_kernel<<<p16, 128, 0, st>>>(p, p16, nk, K16, M[0], nk > 1 ? M[1] : M[0], s[0],
+                                          nk > 1 ? s[1] : 0.0, Md, F);
+  GSI_LAUNCH_CHECK();
+  OzGemmArgs a{};
+  a.U[0] = U[0];
+  a.U[1] = nk > 1 ? U[1] : U[0];
+  a.ne = ne;
+  for (int m = 0; m < ne; ++m) {
+    a.E[m] = E[m];
+    a.ce[m] = ce[m];
+  }
+  a.Md = Md;
+  a.F = F;
+  a.out = out;
+  a.dot_part = dot_part;
+  a.dot_with = dot_with;
+  a.dot_self = dot_self ? 1 : 0;
+  const int ncs = (p16 + 63) / 64;
+  const int NCmax = std::min(64, p16);
+  size_t smem = oz_gemm_smem(K16, NCmax);
+  if (ncs > 1)
+    for (int k = 0; k < nk; ++k)
+      if (U[k] == out) return GSI_ERR_ARG;  // column slices would race on in-place rows
+  GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int64_t ntiles = (n + GM_RT - 1) / GM_RT;
+  int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  int gx = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * per_sm / ncs);
+  gx = std::max(gx, 1);
+  if (nparts) *nparts = gx * ncs;
+  oz_gemm_kernel<<<dim3(gx, ncs), GM_THREADS, smem, st>>>(n, p, p16, nk, K16, a);
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
+int oz_gemm_max_parts(int p) {
+  int ncs = (pad16(p) + 63) / 64;
+  return sm_count() * 2 * ncs;
+}
+
+int oz_gram_blocks(int p, int q, bool sym) {
+  int nbi = (p + 63) / 64, nbj = (q + 63) / 64;
+  return sym ? nbi * (nbi + 1) / 2 : nbi * nbj;
+}
+
+int oz_gram_splits(int64_t n, int p, int q, bool sym) {
+  int nb = oz_gram_blocks(p, q, sym);
+  int64_t chunks = (n + GR_KC - 1) / GR_KC;
+  int s = std::max(1, sm_count() / nb);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(s, chunks));
+}
+
+size_t oz_gram_scratch_bytes(int64_t n, int p, int q, bool sym) {
+  return (size_t)oz_gram_splits(n, p, q, sym) * oz_gram_blocks(p, q, sym) * 4096 * sizeof(float2);
+}
+
+gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bool sym, double* G,
+                   float2* scratch, cudaStream_t st) {
+  if (p < 1 || q < 1 || p > 128 || q > 128 || (sym && p != q)) return GSI_ERR_ARG;
+  const int nbj = (q + 63) / 64;
+  const int nblk = oz_gram_blocks(p, q, sym);
+  const int ns = oz_gram_splits(n, p, q, sym);
+  size_t smem = oz_gram_smem();
+  GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  GSI_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)ns * nblk * 4096 * sizeof(float2), st));
+  oz_gram_kernel<<<dim3(ns, nblk), GR_THREADS, smem, st>>>(n, p, q, U, V, sym ? 1 : 0, nbj, scratch);
+  GSI_LAUNCH_CHECK();
+  oz_gram_reduce_kernel<<<ceil_div(p * q, 256), 256, 0, st>>>(p, q, ns, nblk, sym ? 1 : 0, nbj,
+                                                              scratch, G);
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
+}  // namespace gsi

@@ -1,0 +1,56 @@
+// Internal interface of the df64 block kernels: Ozaki-split tensor-core
+// products (oz.cu) and the df64 SpMM / conversion / reduction kernels (df_blas.cu).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace gsi {
+
+struct OzGemmArgs {
+  const float2* U[2];        // n x p df64 blocks (left operands, concatenated along K)
+  int ne;                    // elementwise terms (0..2)
+  const float2* E[2];        // n x p df64 blocks
+  float2 ce[2];              // df64 scalars of the elementwise terms
+  const __nv_bfloat16* Md;   // digit planes of the right operand
+  const int* F;              // column exponents of the right operand
+  float2* out;               // n x p df64 (may alias an E; may alias a U only when p <= 64)
+  float2* dot_part;          // per-block partials {<out,out>, <out,dot_with>} or null
+  const float2* dot_with;
+  int dot_self;
+};
+
+int pad16(int x);
+size_t oz_rhs_bytes(int p, int nk);
+// OUT = sum_{k<nk} U_k (s_k M_k) + sum_{e<ne} ce_e E_e; M_k float64 p x p (device).
+// rhs_ws: oz_rhs_bytes(p, nk) bytes of device scratch for the right operand's digits.
+// dot_part (optional): 2 * (*nparts) df64 partial sums.
+gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const double* const M[2],
+                   const double s[2], int ne, const float2* const E[2], const float2 ce[2],
+                   float2* out, float2* dot_part, const float2* dot_with, bool dot_self,
+                   void* rhs_ws, cudaStream_t st, int* nparts);
+int oz_gemm_max_parts(int p);
+size_t oz_gram_scratch_bytes(int64_t n, int p, int q, bool sym);
+// G = U^T V (float64 p x q); sym: U == V, only the upper half is computed.
+gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bool sym, double* G,
+                   float2* scratch, cudaStream_t st);
+
+// df64 block helpers (df_blas.cu)
+gsi_status df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);
+gsi_status df_to_f64(int64_t count, const float2* x, double* y, cudaStream_t st);
+gsi_status df_spmm_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx, const float2* val,
+                       int p, const float2* X, float2* W, cudaStream_t st);
+gsi_status df_spmm_sell(int64_t nchunks, int C, const int64_t* perm, const int64_t* chunk_ptr,
+                        const int64_t* chunk_len, const int32_t* scol, const float2* sval, int p,
+                        const float2* X, float2* W, cudaStream_t st);
+int df_dots_blocks(int64_t count);
+// out[0] = <A0,B0>, out[1] = <A1,B1> (float64), out[2] = max_r sum_j |R[r,j]| (if R)
+gsi_status df_dots(int64_t n, int p, const float2* A0, const float2* B0, const float2* A1,
+                   const float2* B1, const float2* R, double* out, float2* scratch,
+                   cudaStream_t st);
+// y = a*x + b*y elementwise (df64 scalars)
+gsi_status df_axpby(int64_t count, float2 a, const float2* x, float2 b, float2* y, cudaStream_t st);
+// sum of df64 partial pairs into out[0..1] (float64)
+gsi_status df_sum_parts(int nparts, const float2* parts, double* out, cudaStream_t st);
+
+}  // namespace gsi

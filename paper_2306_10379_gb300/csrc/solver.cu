@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "blas_f64.cuh"
@@ -25,6 +26,9 @@
 namespace gsi {
 
 static thread_local char g_last_error[256] = "";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(const char* msg) {
   snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
@@ -384,6 +388,7 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
     CK(cuda_status_ok(cudaMemcpyAsync(c->val, A->val, c->nnz * sizeof(double), kind, c->st)));
     if (c->sign < 0 && c->nnz > 0) {
       scale_kernel<<<ceil_div(c->nnz, 256), 256, 0, c->st>>>(c->nnz, -1.0, c->val);
+      note_launch();
       CK(cuda_status_ok(cudaGetLastError()));
     }
     if (c->fmt == GSI_SELL) {
@@ -440,6 +445,7 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       unsigned long long* d_mx = (unsigned long long*)c->dout;
       CK(cuda_status_ok(cudaMemsetAsync(d_mx, 0, 8, c->st)));
       csr_absmax_kernel<<<ceil_div(n, 256), 256, 0, c->st>>>(n, c->rowptr, c->val, d_mx);
+      note_launch();
       CK(cuda_status_ok(cudaGetLastError()));
       CK(readback(c, c->dout, 1));
       c->anorm = c->host[0];

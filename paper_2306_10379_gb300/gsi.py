@@ -24,7 +24,7 @@ EXPORTED = [
     "gsi_default_opts", "gsi_create", "gsi_step", "gsi_solve", "gsi_get_basis", "gsi_state_ptrs",
     "gsi_destroy", "gsi_status_str", "gsi_last_error", "gsi_spmm_csr", "gsi_sell_size",
     "gsi_csr_to_sell", "gsi_spmm_sell", "gsi_gram", "gsi_residual", "gsi_linesearch",
-    "gsi_retract",
+    "gsi_retract", "gsi_df_spmm_csr", "gsi_oz_gemm", "gsi_oz_gram",
 ]
 
 
@@ -88,6 +88,9 @@ def _lib():
             "gsi_residual": [i64, i32, vp, vp, vp, vp, vp],
             "gsi_linesearch": [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
             "gsi_retract": [i64, i32, dbl, vp, vp, vp, vp, vp, vp],
+            "gsi_df_spmm_csr": [i64, vp, vp, vp, i32, vp, vp, vp],
+            "gsi_oz_gemm": [i64, i32, i32, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp, vp, vp],
+            "gsi_oz_gram": [i64, i32, i32, vp, vp, i32, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -210,6 +213,59 @@ def retract(t, M, X, D, Y, W, stream=None):
     f = torch.float64
     _check(lib().gsi_retract(n, p, float(t), _dptr(M, f, (p, p)), _dptr(X, f), _dptr(D, f, (n, p)),
                              _dptr(Y, f, (n, p)), _dptr(W, f, (n, p)), _stream(stream)), "gsi_retract")
+
+
+# ----------------------------------------------------------------------------
+# df64 kernels: a df64 tensor is float32 with a trailing dimension of 2 (hi, lo)
+# ----------------------------------------------------------------------------
+
+def to_df(x):
+    """float64 numpy array -> float32 array with trailing (hi, lo) axis."""
+    x = np.asarray(x, dtype=np.float64)
+    h = x.astype(np.float32)
+    l = (x - h.astype(np.float64)).astype(np.float32)
+    return np.stack([h, l], axis=-1)
+
+
+def from_df(d):
+    d = np.asarray(d)
+    return d[..., 0].astype(np.float64) + d[..., 1].astype(np.float64)
+
+
+def df_spmm_csr(rowptr, colidx, val_df, X_df, W_df, stream=None):
+    import torch
+    n, p = X_df.shape[0], X_df.shape[1]
+    f = torch.float32
+    _check(lib().gsi_df_spmm_csr(n, _dptr(rowptr, torch.int64), _dptr(colidx, torch.int32),
+                                 _dptr(val_df, f), p, _dptr(X_df, f), _dptr(W_df, f, (n, p, 2)),
+                                 _stream(stream)), "gsi_df_spmm_csr")
+
+
+def oz_gemm(U0, M0, out, s0=1.0, U1=None, M1=None, s1=0.0, E=(), c=(), stream=None):
+    import torch
+    n, p = U0.shape[0], U0.shape[1]
+    f, d = torch.float32, torch.float64
+    nk = 2 if U1 is not None else 1
+    cc = np.zeros(4, np.float32)  # host memory: the scalars are read by the host
+    for m, cm in enumerate(c):
+        cc[2 * m:2 * m + 2] = to_df(np.float64(cm))
+    E = list(E) + [None] * (2 - len(E))
+    _check(lib().gsi_oz_gemm(n, p, nk, _dptr(U0, f), _dptr(U1, f) if U1 is not None else None,
+                             _dptr(M0, d, (p, p)), _dptr(M1, d, (p, p)) if M1 is not None else None,
+                             float(s0), float(s1), len([e for e in E if e is not None]),
+                             _dptr(E[0], f) if E[0] is not None else None,
+                             _dptr(E[1], f) if E[1] is not None else None,
+                             ctypes.c_void_p(cc.ctypes.data),
+                             _dptr(out, f, (n, p, 2)), _stream(stream)), "gsi_oz_gemm")
+
+
+def oz_gram(U, V, G, sym=False, stream=None):
+    import torch
+    n, p = U.shape[0], U.shape[1]
+    q = V.shape[1]
+    f = torch.float32
+    _check(lib().gsi_oz_gram(n, p, q, _dptr(U, f), _dptr(V, f), 1 if sym else 0,
+                             _dptr(G, torch.float64, (p, q)), _stream(stream)), "gsi_oz_gram")
 
 
 # ----------------------------------------------------------------------------

@@ -1,0 +1,129 @@
+"""Parity of the df64 / Ozaki-split tensor-core kernels with the CPU oracle.
+
+Inputs are float64 values rounded to df64 (hi + lo, 48-bit significand); the
+oracle computes with those exact values in float64. Bounds follow the
+construction: operands are cut at 2^-49 of a row/column/chunk maximum, so
+errors are measured against products of those maxima.
+"""
+import numpy as np
+import pytest
+
+from oracle import gsi_oracle as O
+from paper_2306_10379_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    from paper_2306_10379_gb300 import build, gsi
+    build.build()
+    return torch, gsi
+
+
+def _df_dev(torch, gsi, x):
+    return torch.from_numpy(gsi.to_df(x)).cuda()
+
+
+def _exact(gsi, x):
+    return gsi.from_df(gsi.to_df(x))
+
+
+@pytest.mark.parametrize("p", [1, 7, 64])
+def test_df_spmm(G, p):
+    torch, gsi = G
+    A = I.er_laplacian(20011, 3)
+    X = _exact(gsi, I.start_block(A.n, p, 1))
+    val = _exact(gsi, A.val * (1 + 1e-9 * np.arange(A.nnz) / A.nnz))  # non-integer values
+    S = O.csr_operator(A.n, A.rowptr, A.colidx, val)
+    W = torch.empty((A.n, p, 2), dtype=torch.float32, device="cuda")
+    gsi.df_spmm_csr(torch.from_numpy(A.rowptr).cuda(), torch.from_numpy(A.colidx).cuda(),
+                    _df_dev(torch, gsi, val), _df_dev(torch, gsi, X), W)
+    got = gsi.from_df(W.cpu().numpy())
+    ref = O.spmm(S, X)
+    assert np.all(np.abs(got - ref) <= 1e-13 * O.spmm(abs(S), np.abs(X)))
+
+
+@pytest.mark.parametrize("n,p,nk,ne", [(1, 1, 1, 0), (33, 8, 1, 1), (1000, 17, 2, 2), (100003, 64, 1, 1),
+                                       (50001, 64, 2, 0), (20000, 100, 1, 2), (20000, 128, 2, 1),
+                                       (777, 5, 2, 2)])
+def test_oz_gemm(G, n, p, nk, ne):
+    torch, gsi = G
+    rng = np.random.default_rng(n + p)
+    U = [_exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-3, 3, (n, 1)))) for _ in range(nk)]
+    M = [rng.standard_normal((p, p)) * np.exp(rng.uniform(-2, 2, (1, p))) for _ in range(nk)]
+    s = [0.7, -1.3][:nk]
+    E = [_exact(gsi, rng.standard_normal((n, p))) for _ in range(ne)]
+    c = [0.3, -2.5][:ne]
+    ref = sum(sk * Uk @ Mk for sk, Uk, Mk in zip(s, U, M)) + sum(cm * Em for cm, Em in zip(c, E))
+    out = torch.zeros((n, p, 2), dtype=torch.float32, device="cuda")
+    Ud = [_df_dev(torch, gsi, u) for u in U]
+    Md = [torch.from_numpy(m).cuda() for m in M]
+    gsi.oz_gemm(Ud[0], Md[0], out, s0=s[0], U1=Ud[1] if nk > 1 else None, M1=Md[1] if nk > 1 else None,
+                s1=s[1] if nk > 1 else 0.0, E=[_df_dev(torch, gsi, e) for e in E], c=c)
+    got = gsi.from_df(out.cpu().numpy())
+    # bound: K terms, each cut at 2^-49 of its row max times its column max
+    bound = sum(abs(sk) * np.abs(Uk).max(1, keepdims=True) * np.abs(Mk).max(0, keepdims=True)
+                for sk, Uk, Mk in zip(s, U, M)) * (nk * p) * 2.0 ** -44
+    bound = bound + sum(abs(cm) * np.abs(Em) for cm, Em in zip(c, E)) * 2.0 ** -46
+    assert np.all(np.abs(got - ref) <= bound + 1e-300)
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_oz_gemm_exact_on_grid(G):
+    """Operands on the digit grid (small integers times a row power of two)
+    are represented exactly, so the products are exact: bit-equal results."""
+    torch, gsi = G
+    rng = np.random.default_rng(7)
+    n, p = 4099, 64
+    U = rng.integers(-2 ** 20, 2 ** 20, (n, p)).astype(np.float64) * 2.0 ** rng.integers(-10, 10, (n, 1))
+    M = rng.integers(-2 ** 20, 2 ** 20, (p, p)).astype(np.float64) * 2.0 ** -20
+    out = torch.zeros((n, p, 2), dtype=torch.float32, device="cuda")
+    gsi.oz_gemm(_df_dev(torch, gsi, U), torch.from_numpy(M).cuda(), out)
+    ref = U @ M
+    got = gsi.from_df(out.cpu().numpy())
+    # exact integers up to 2^46 * scale: float64 reference is exact too
+    assert np.array_equal(got, ref)
+
+
+def test_oz_gemm_in_place(G):
+    torch, gsi = G
+    rng = np.random.default_rng(9)
+    n, p = 3001, 32
+    U = _exact(gsi, rng.standard_normal((n, p)))
+    M = rng.standard_normal((p, p))
+    E = _exact(gsi, rng.standard_normal((n, p)))
+    Ud = _df_dev(torch, gsi, U)
+    Ed = _df_dev(torch, gsi, E)
+    gsi.oz_gemm(Ud, torch.from_numpy(M).cuda(), Ud, E=[Ed], c=[1.0])  # U <- U M + E
+    assert np.linalg.norm(gsi.from_df(Ud.cpu().numpy()) - (U @ M + E)) <= 1e-13 * np.linalg.norm(U @ M)
+    gsi.oz_gemm(_df_dev(torch, gsi, U), torch.from_numpy(M).cuda(), Ed, E=[Ed], c=[-1.0])  # E <- U M - E
+    assert np.linalg.norm(gsi.from_df(Ed.cpu().numpy()) - (U @ M - E)) <= 1e-13 * np.linalg.norm(U @ M)
+
+
+@pytest.mark.parametrize("n,p,q,sym", [(1, 1, 1, False), (63, 8, 8, True), (65, 8, 3, False),
+                                       (10007, 64, 64, True), (10007, 64, 64, False),
+                                       (200001, 64, 64, True), (30000, 128, 128, True),
+                                       (30000, 65, 128, False), (5000, 100, 17, False)])
+def test_oz_gram(G, n, p, q, sym):
+    torch, gsi = G
+    rng = np.random.default_rng(n * 3 + p)
+    U = _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-4, 4, (1, p))))
+    V = U if sym else _exact(gsi, rng.standard_normal((n, q)) * np.exp(rng.uniform(-4, 4, (1, q))))
+    Ud = _df_dev(torch, gsi, U)
+    Vd = Ud if sym else _df_dev(torch, gsi, V)
+    Gm = torch.full((p, q), np.nan, dtype=torch.float64, device="cuda")
+    gsi.oz_gram(Ud, Vd, Gm, sym=sym)
+    got = Gm.cpu().numpy()
+    ref = O.gram(U, V)
+    absprod = np.abs(U).T @ np.abs(V)
+    # per 64-row chunk each product is cut at 2^-49 of the chunk column maxima
+    chunk_bound = np.zeros((p, q))
+    for r0 in range(0, n, 64):
+        cu = np.abs(U[r0:r0 + 64]).max(0)
+        cv = np.abs(V[r0:r0 + 64]).max(0)
+        chunk_bound += np.outer(cu, cv) * min(64, n - r0)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -44 * chunk_bound + 2.0 ** -46 * absprod)
+    if sym:
+        assert np.array_equal(got, got.T)
