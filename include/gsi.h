@@ -46,6 +46,11 @@ typedef enum {
 
 typedef enum { GSI_CSR = 0, GSI_SELL = 1 } gsi_format;
 typedef enum { GSI_SD = 0, GSI_CG = 1 } gsi_method;
+/* Arithmetic of the n x p block work. GSI_PREC_DF64: blocks stored as
+ * float32 pairs (48-bit significand), products on the BF16 tensor cores with
+ * error-free digit splitting (float64-class results); GSI_PREC_F64: native
+ * float64 on the float64 pipe. The p x p step is float64 in both. */
+typedef enum { GSI_PREC_DF64 = 0, GSI_PREC_F64 = 1 } gsi_precision;
 
 /* Sparse symmetric A in full CSR storage (both triangles).
  * rowptr: n+1 int64, colidx: nnz int32 (0-based), val: nnz float64.
@@ -74,6 +79,7 @@ typedef struct {
   int32_t k_restart;       /* CG restart period; 0 = never (default) */
   int32_t recompute_every; /* explicit Y = AX every k iterations; 0 = only when the step is tiny */
   int32_t explicit_ax;     /* 1: explicit AX every iteration ("RCG(+)", Sec. 6.4) */
+  int32_t precision;       /* gsi_precision, default GSI_PREC_DF64 */
 } gsi_opts;
 
 typedef struct {
@@ -121,9 +127,35 @@ gsi_status gsi_solve(gsi_ctx* ctx, gsi_info* info);
  * host. The context's own iterate is not changed. */
 gsi_status gsi_get_basis(gsi_ctx* ctx, double* X, double* evals, int32_t to_device);
 
+/* Restart from a new start block with the same operator, p and options,
+ * reusing the context's device memory (X0 as in gsi_create). */
+gsi_status gsi_reset(gsi_ctx* ctx, const double* X0, int32_t X0_on_device);
+
 /* Device pointers of the context's current iterate X and Y = AX (n x p
- * row-major), valid until the next call on ctx. For tests and benchmarks. */
-gsi_status gsi_state_ptrs(gsi_ctx* ctx, double** X, double** Y);
+ * row-major; float64 for GSI_PREC_F64, df64 pairs for GSI_PREC_DF64), valid
+ * until the next call on ctx. For tests and benchmarks. */
+gsi_status gsi_state_ptrs(gsi_ctx* ctx, void** X, void** Y);
+
+/* Kernel classes for gsi_profile_read. */
+typedef enum {
+  GSI_K_SPMM = 0,      /* block matvec A*Z */
+  GSI_K_GRAM = 1,      /* Gram products U^T V */
+  GSI_K_BLOCKMUL = 2,  /* n x p blocks times p x p matrices, fused elementwise terms */
+  GSI_K_SMALL = 3,     /* p x p step: eigensolver, line search, polar normaliser */
+  GSI_K_REDUCE = 4,    /* norms */
+  GSI_K_COUNT = 5
+} gsi_kernel_class;
+
+/* on != 0: record CUDA events around every kernel group this context launches
+ * (on its stream) and accumulate per-class device time; resets the totals. */
+gsi_status gsi_profile_enable(gsi_ctx* ctx, int32_t on);
+/* Totals since gsi_profile_enable for class k: launch groups, device ms, and
+ * the algorithmic bytes / flops of those launches (float64-equivalent:
+ * 8 bytes per block entry, 12 bytes per nonzero, 2 flops per multiply-add). */
+gsi_status gsi_profile_read(gsi_ctx* ctx, int32_t k, int64_t* launches, double* total_ms,
+                            double* alg_bytes, double* alg_flops);
+/* Number of kernels this library has launched in this process. */
+int64_t gsi_launch_count(void);
 
 gsi_status gsi_destroy(gsi_ctx* ctx);
 

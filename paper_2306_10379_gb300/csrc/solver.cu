@@ -22,6 +22,8 @@
 #include <vector>
 
 #include "blas_f64.cuh"
+#include "df.cuh"
+#include "oz.cuh"
 
 namespace gsi {
 
@@ -83,15 +85,19 @@ __global__ void csr_absmax_kernel(int64_t n, const int64_t* rowptr, const double
 
 using namespace gsi;
 
+// Block element: float64 (precision GSI_PREC_F64) or df64 float2 (GSI_PREC_DF64);
+// both are 8 bytes, so every n x p buffer has the same size in both modes.
 struct gsi_ctx {
   cudaStream_t st = nullptr;
   int64_t n = 0, nnz = 0;
   int p = 0;
   gsi_opts o{};
+  bool emu = true;
   int fmt = GSI_CSR;
   int64_t* rowptr = nullptr;
   int32_t* colidx = nullptr;
-  double* val = nullptr;
+  double* val = nullptr;    // float64 values (native mode and Rayleigh-Ritz)
+  float2* vdf = nullptr;    // df64 values
   int C = 32;
   int64_t nchunks = 0;
   int64_t* perm = nullptr;
@@ -99,13 +105,17 @@ struct gsi_ctx {
   int64_t* chunk_len = nullptr;
   int32_t* scol = nullptr;
   double* sval = nullptr;
+  float2* sdf = nullptr;
   double anorm = 0.0;
   double sign = 1.0;
-  double *X = nullptr, *Y = nullptr, *R = nullptr, *Rp = nullptr, *D = nullptr, *P = nullptr,
-         *W = nullptr;
+  void *X = nullptr, *Y = nullptr, *R = nullptr, *Rp = nullptr, *D = nullptr, *P = nullptr,
+       *W = nullptr, *Xn = nullptr, *Yn = nullptr;
   double* pp = nullptr;  // p x p matrices
   double *Cm, *Bm, *Gm, *Zm, *XXm, *XDm, *Km, *Mm, *out, *dout;
   double* gram_ws = nullptr;
+  float2* oz_gram_ws = nullptr;
+  void* oz_rhs_ws = nullptr;
+  float2* oz_parts = nullptr;
   double* dots_ws = nullptr;
   double* small_ws = nullptr;
   double* host = nullptr;  // pinned readback buffer
@@ -114,6 +124,19 @@ struct gsi_ctx {
   int iters = 0, matvecs = 0, restarts = 0, last_evals = 0;
   bool y_fresh = true, have_prev = false, converged = false;
   double rr_prev = 0.0, res0_inf = -1.0, last_t = 0.0, rel = NAN, rel_inf = NAN;
+  // per-class timing (CUDA events on the context's stream)
+  bool prof = false;
+  struct Cls {
+    long long launches = 0;
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
+  } cls[GSI_K_COUNT];
+  std::vector<cudaEvent_t> pool;
+  struct Pending {
+    int k;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  cudaEvent_t cur = nullptr;
 };
 
 namespace {
@@ -125,75 +148,202 @@ gsi_status dev_alloc(gsi_ctx* c, void** p, size_t bytes) {
   return GSI_OK;
 }
 
-gsi_status matvec(gsi_ctx* c, const double* in, double* outp) {
-  c->matvecs++;
-  if (c->fmt == GSI_SELL)
-    return spmm_sell(c->n, c->nchunks, c->C, c->perm, c->chunk_ptr, c->chunk_len, c->scol,
-                     c->sval, c->p, in, outp, c->st);
-  return spmm_csr(c->n, c->rowptr, c->colidx, c->val, c->p, in, outp, c->st);
+cudaEvent_t pool_get(gsi_ctx* c) {
+  if (c->pool.empty()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t e = c->pool.back();
+  c->pool.pop_back();
+  return e;
 }
 
-gsi_status G(gsi_ctx* c, const double* U, const double* V, double* out) {
-  return gram(c->n, c->p, c->p, U, V, out, c->gram_ws, c->st);
+void prof_begin(gsi_ctx* c) {
+  if (!c->prof) return;
+  c->cur = pool_get(c);
+  cudaEventRecord(c->cur, c->st);
+}
+
+void prof_end(gsi_ctx* c, int k, double bytes, double flops) {
+  if (!c->prof || !c->cur) return;
+  cudaEvent_t e = pool_get(c);
+  cudaEventRecord(e, c->st);
+  c->pending.push_back({k, c->cur, e});
+  c->cur = nullptr;
+  c->cls[k].launches++;
+  c->cls[k].bytes += bytes;
+  c->cls[k].flops += flops;
+}
+
+// after a stream synchronisation: fold finished event pairs into the totals
+void prof_harvest(gsi_ctx* c) {
+  for (auto& pe : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) c->cls[pe.k].ms += ms;
+    c->pool.push_back(pe.a);
+    c->pool.push_back(pe.b);
+  }
+  c->pending.clear();
 }
 
 gsi_status readback(gsi_ctx* c, const double* src, int count) {
   GSI_CUDA_TRY(cudaMemcpyAsync(c->host, src, count * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  prof_harvest(c);
   return GSI_OK;
 }
 
-// X <- X M (in place), M = (X^T X)^{-1/2}.
+double blk_bytes(gsi_ctx* c) { return 8.0 * (double)c->n * c->p; }
+
+// ---- block operations, float64 or df64 ------------------------------------
+
+gsi_status op_matvec(gsi_ctx* c, const void* in, void* outp) {
+  c->matvecs++;
+  prof_begin(c);
+  gsi_status s;
+  double bytes;
+  if (c->fmt == GSI_SELL) {
+    int64_t slots = c->nchunks * c->C;
+    bytes = 12.0 * (double)c->nnz + 8.0 * slots + 2 * blk_bytes(c);
+    s = c->emu ? df_spmm_sell(c->nchunks, c->C, c->perm, c->chunk_ptr, c->chunk_len, c->scol,
+                              c->sdf, c->p, (const float2*)in, (float2*)outp, c->st)
+               : spmm_sell(c->n, c->nchunks, c->C, c->perm, c->chunk_ptr, c->chunk_len, c->scol,
+                           c->sval, c->p, (const double*)in, (double*)outp, c->st);
+  } else {
+    bytes = 12.0 * (double)c->nnz + 8.0 * (c->n + 1) + 2 * blk_bytes(c);
+    s = c->emu ? df_spmm_csr(c->n, c->rowptr, c->colidx, c->vdf, c->p, (const float2*)in,
+                             (float2*)outp, c->st)
+               : spmm_csr(c->n, c->rowptr, c->colidx, c->val, c->p, (const double*)in,
+                          (double*)outp, c->st);
+  }
+  prof_end(c, GSI_K_SPMM, bytes, 2.0 * c->nnz * c->p);
+  return s;
+}
+
+gsi_status op_gram(gsi_ctx* c, const void* U, const void* V, bool sym, double* G) {
+  prof_begin(c);
+  gsi_status s;
+  if (c->emu) {
+    s = oz_gram(c->n, c->p, c->p, (const float2*)U, (const float2*)V, sym && U == V, G,
+                c->oz_gram_ws, c->st);
+    if (s == GSI_OK && sym && U != V) {
+      symmetrize_kernel<<<ceil_div(c->p * c->p, 256), 256, 0, c->st>>>(c->p, G);
+      note_launch();
+    }
+  } else {
+    s = gram(c->n, c->p, c->p, (const double*)U, (const double*)V, G, c->gram_ws, c->st);
+    if (s == GSI_OK && sym) {
+      symmetrize_kernel<<<ceil_div(c->p * c->p, 256), 256, 0, c->st>>>(c->p, G);
+      note_launch();
+    }
+  }
+  prof_end(c, GSI_K_GRAM, (U == V ? 1 : 2) * blk_bytes(c), 2.0 * c->n * c->p * c->p);
+  return s;
+}
+
+// out = s0 U0 M0 (+ s1 U1 M1) + c0 E0 (+ c1 E1); optional dots (emu: fused;
+// f64: separate pass) <out,out> -> dout[0], <out,dw> -> dout[1].
+gsi_status op_blockmul(gsi_ctx* c, int nk, const void* U0, const double* M0, double s0,
+                       const void* U1, const double* M1, double s1, int ne, const void* E0,
+                       double c0, const void* E1, double c1, void* outp, bool dot_self,
+                       const void* dw) {
+  prof_begin(c);
+  gsi_status s;
+  const bool want = dot_self || dw;
+  if (c->emu) {
+    const float2* U[2] = {(const float2*)U0, (const float2*)(U1 ? U1 : U0)};
+    const double* M[2] = {M0, M1 ? M1 : M0};
+    double sc[2] = {s0, s1};
+    const float2* E[2] = {(const float2*)E0, (const float2*)E1};
+    float2 ce[2] = {df_from_double(c0), df_from_double(c1)};
+    int np = 0;
+    s = oz_gemm(c->n, c->p, nk, U, M, sc, ne, E, ce, (float2*)outp, want ? c->oz_parts : nullptr,
+                (const float2*)dw, dot_self, c->oz_rhs_ws, c->st, &np);
+    if (s == GSI_OK && want) s = df_sum_parts(np, c->oz_parts, c->dout, c->st);
+  } else {
+    RowMulArgs a{};
+    a.nk = nk;
+    a.U[0] = (const double*)U0;
+    a.M[0] = M0;
+    a.s[0] = s0;
+    a.U[1] = (const double*)U1;
+    a.M[1] = M1;
+    a.s[1] = s1;
+    a.ne = ne;
+    a.E[0] = (const double*)E0;
+    a.c[0] = c0;
+    a.E[1] = (const double*)E1;
+    a.c[1] = c1;
+    s = rowmul(c->n, c->p, a, (double*)outp, c->st);
+    if (s == GSI_OK && want)
+      s = dots(c->n, c->p, 2, (const double*)outp, (const double*)outp, (const double*)outp,
+               (const double*)(dw ? dw : outp), nullptr, c->dout, c->dots_ws, c->st);
+  }
+  prof_end(c, GSI_K_BLOCKMUL, (nk + ne + 1) * blk_bytes(c), 2.0 * c->n * c->p * (double)nk * c->p);
+  return s;
+}
+
+// max_r sum_j |R[r, j]| -> dout[2]
+gsi_status op_rowinf(gsi_ctx* c, const void* Rb) {
+  prof_begin(c);
+  gsi_status s;
+  if (c->emu)
+    s = df_dots(c->n, c->p, nullptr, nullptr, nullptr, nullptr, (const float2*)Rb, c->dout,
+                (float2*)c->dots_ws, c->st);
+  else
+    s = dots(c->n, c->p, 0, nullptr, nullptr, nullptr, nullptr, (const double*)Rb, c->dout,
+             c->dots_ws, c->st);
+  prof_end(c, GSI_K_REDUCE, blk_bytes(c), 0.0);
+  return s;
+}
+
+gsi_status op_small(gsi_ctx* c, int mode, const double* B, const double* Zp) {
+  prof_begin(c);
+  gsi_status s = small_step(mode, c->p, c->Cm, B, c->Gm, Zp, c->XXm, c->XDm, c->Mm, c->out,
+                            c->small_ws, c->st);
+  prof_end(c, GSI_K_SMALL, 0.0, 0.0);
+  return s;
+}
+
+// X <- X M (M = (X^T X)^{-1/2}), twice
 gsi_status orthonormalize(gsi_ctx* c) {
   for (int pass = 0; pass < 2; ++pass) {
-    GSI_TRY(G(c, c->X, c->X, c->Bm));
-    GSI_TRY(small_step(1, c->p, nullptr, c->Bm, nullptr, nullptr, nullptr, nullptr, c->Mm, c->out,
-                       c->small_ws, c->st));
+    GSI_TRY(op_gram(c, c->X, c->X, true, c->Bm));
+    GSI_TRY(op_small(c, 1, c->Bm, c->Bm));
     GSI_TRY(readback(c, c->out, 5));
     if (c->host[3] != 0.0) return GSI_ERR_BREAKDOWN;
-    RowMulArgs a{};
-    a.nk = 1;
-    a.U[0] = c->X;
-    a.M[0] = c->Mm;
-    a.s[0] = 1.0;
-    GSI_TRY(rowmul(c->n, c->p, a, c->X, c->st));
+    GSI_TRY(op_blockmul(c, 1, c->X, c->Mm, 1.0, nullptr, nullptr, 0.0, 0, nullptr, 0.0, nullptr,
+                        0.0, c->Xn, false, nullptr));
+    std::swap(c->X, c->Xn);
   }
   return GSI_OK;
 }
 
 // One iteration; returns GSI_OK and sets *stop when the stopping test holds.
 gsi_status iterate(gsi_ctx* c, bool* stop) {
-  const int p = c->p;
-  const int64_t n = c->n;
   const bool cg = c->o.method == GSI_CG;
   *stop = false;
   double rr = 0.0, rp = 0.0, rinf = 0.0;
   for (;;) {
-    GSI_TRY(G(c, c->X, c->Y, c->Cm));
-    symmetrize_kernel<<<ceil_div(p * p, 256), 256, 0, c->st>>>(p, c->Cm);
-    GSI_LAUNCH_CHECK();
-    RowMulArgs a{};
-    a.nk = 1;
-    a.U[0] = c->X;
-    a.M[0] = c->Cm;
-    a.s[0] = -1.0;
-    a.ne = 1;
-    a.E[0] = c->Y;
-    a.c[0] = 1.0;
-    GSI_TRY(rowmul(n, p, a, c->R, c->st));
-    bool want_rp = cg && c->have_prev;
-    GSI_TRY(dots(n, p, want_rp ? 2 : 1, c->R, c->R, c->R, c->Rp, c->R, c->dout, c->dots_ws, c->st));
-    GSI_TRY(readback(c, c->dout, 3));
+    GSI_TRY(op_gram(c, c->X, c->Y, true, c->Cm));  // C = X^T A X, symmetric
+    const bool want_rp = cg && c->have_prev;
+    // R = Y - X C with <R,R> and <R,R_prev>
+    GSI_TRY(op_blockmul(c, 1, c->X, c->Cm, -1.0, nullptr, nullptr, 0.0, 1, c->Y, 1.0, nullptr, 0.0,
+                        c->R, true, want_rp ? c->Rp : nullptr));
+    GSI_TRY(readback(c, c->dout, 2));
     rr = c->host[0];
-    rp = c->host[1];
-    rinf = c->host[2];
+    rp = want_rp ? c->host[1] : 0.0;
+    GSI_TRY(op_rowinf(c, c->R));
+    GSI_TRY(readback(c, c->dout + 2, 1));
+    rinf = c->host[0];
     if (!isfinite(rr)) return GSI_ERR_NONFINITE;
     if (c->res0_inf < 0.0) c->res0_inf = rinf;
     c->rel = sqrt(rr) / c->anorm;
     c->rel_inf = c->res0_inf > 0.0 ? rinf / c->res0_inf : 0.0;
     if (c->rel <= c->o.tol || c->iters >= c->o.max_iters) {
       if (!c->y_fresh) {  // the final residual is always taken with an explicit AX
-        GSI_TRY(matvec(c, c->X, c->Y));
+        GSI_TRY(op_matvec(c, c->X, c->Y));
         c->y_fresh = true;
         continue;
       }
@@ -204,47 +354,36 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
     break;
   }
   // search direction
-  const double* Dp = c->R;
+  const void* Dp = c->R;
   bool restarted = false;
   if (cg) {
     if (c->have_prev) {
       double b = (rr - rp) / c->rr_prev;
-      GSI_TRY(G(c, c->X, c->P, c->Km));
-      RowMulArgs a{};
-      a.nk = 1;
-      a.U[0] = c->X;
-      a.M[0] = c->Km;
-      a.s[0] = -b;
-      a.ne = 2;
-      a.E[0] = c->R;
-      a.c[0] = 1.0;
-      a.E[1] = c->P;
-      a.c[1] = b;
-      GSI_TRY(rowmul(n, p, a, c->D, c->st));
-      GSI_TRY(dots(n, p, 1, c->D, c->R, nullptr, nullptr, nullptr, c->dout, c->dots_ws, c->st));
-      GSI_TRY(readback(c, c->dout, 1));
+      GSI_TRY(op_gram(c, c->X, c->P, false, c->Km));
+      // D = R + b P - X (b K), with <D, R>
+      GSI_TRY(op_blockmul(c, 1, c->X, c->Km, -b, nullptr, nullptr, 0.0, 2, c->R, 1.0, c->P, b,
+                          c->D, false, c->R));
+      GSI_TRY(readback(c, c->dout + 1, 1));
       bool due = c->o.k_restart > 0 && c->iters % c->o.k_restart == 0;
       if (due || !(c->host[0] > 0.0)) restarted = true;
     }
     if (!c->have_prev || restarted) {
-      GSI_CUDA_TRY(cudaMemcpyAsync(c->D, c->R, (size_t)n * p * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, c->st));
+      GSI_CUDA_TRY(cudaMemcpyAsync(c->D, c->R, (size_t)blk_bytes(c), cudaMemcpyDeviceToDevice, c->st));
     }
     if (restarted) c->restarts++;
     Dp = c->D;
   }
-  GSI_TRY(matvec(c, Dp, c->W));
-  GSI_TRY(G(c, Dp, Dp, c->Bm));
-  GSI_TRY(G(c, Dp, c->W, c->Gm));
+  GSI_TRY(op_matvec(c, Dp, c->W));
+  GSI_TRY(op_gram(c, Dp, Dp, true, c->Bm));
+  GSI_TRY(op_gram(c, Dp, c->W, true, c->Gm));
   const double* Zp = c->Bm;
   if (cg) {
-    GSI_TRY(G(c, Dp, c->R, c->Zm));
+    GSI_TRY(op_gram(c, Dp, c->R, false, c->Zm));
     Zp = c->Zm;
   }
-  GSI_TRY(G(c, c->X, c->X, c->XXm));
-  GSI_TRY(G(c, c->X, Dp, c->XDm));
-  GSI_TRY(small_step(0, p, c->Cm, c->Bm, c->Gm, Zp, c->XXm, c->XDm, c->Mm, c->out, c->small_ws,
-                     c->st));
+  GSI_TRY(op_gram(c, c->X, c->X, true, c->XXm));
+  GSI_TRY(op_gram(c, c->X, Dp, false, c->XDm));
+  GSI_TRY(op_small(c, 0, c->Bm, Zp));
   GSI_TRY(readback(c, c->out, 5));
   const double t = c->host[0];
   c->last_t = t;
@@ -254,29 +393,16 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
   const double bmax = c->host[4];
   bool recompute = c->o.explicit_ax || t * sqrt(std::max(bmax, 0.0)) < 1e3 * 2.220446049250313e-16 ||
                    (c->o.recompute_every > 0 && (c->iters + 1) % c->o.recompute_every == 0);
-  {
-    RowMulArgs a{};
-    a.nk = 2;
-    a.U[0] = c->X;
-    a.M[0] = c->Mm;
-    a.s[0] = 1.0;
-    a.U[1] = Dp;
-    a.M[1] = c->Mm;
-    a.s[1] = t;
-    GSI_TRY(rowmul(n, p, a, c->X, c->st));
-  }
+  // X <- (X + tD) M, Y <- (Y + tW) M (Eq. (save_matvec)) or Y <- A X
+  GSI_TRY(op_blockmul(c, 2, c->X, c->Mm, 1.0, Dp, c->Mm, t, 0, nullptr, 0.0, nullptr, 0.0, c->Xn,
+                      false, nullptr));
+  std::swap(c->X, c->Xn);
   if (recompute) {
-    GSI_TRY(matvec(c, c->X, c->Y));
+    GSI_TRY(op_matvec(c, c->X, c->Y));
   } else {
-    RowMulArgs a{};
-    a.nk = 2;
-    a.U[0] = c->Y;
-    a.M[0] = c->Mm;
-    a.s[0] = 1.0;
-    a.U[1] = c->W;
-    a.M[1] = c->Mm;
-    a.s[1] = t;
-    GSI_TRY(rowmul(n, p, a, c->Y, c->st));
+    GSI_TRY(op_blockmul(c, 2, c->Y, c->Mm, 1.0, c->W, c->Mm, t, 0, nullptr, 0.0, nullptr, 0.0,
+                        c->Yn, false, nullptr));
+    std::swap(c->Y, c->Yn);
   }
   c->y_fresh = recompute;
   c->iters++;
@@ -308,6 +434,30 @@ void fill_info(gsi_ctx* c, gsi_info* info) {
   info->trace = c->sign * tr;
 }
 
+// load X0 (float64, host or device), orthonormalise, Y = A X, clear the state
+gsi_status start(gsi_ctx* c, const double* X0, int on_device) {
+  const size_t blk = (size_t)blk_bytes(c);
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (c->emu) {
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->W, X0, blk, kind, c->st));  // float64 staging in W
+    GSI_TRY(df_from_f64(c->n * c->p, (const double*)c->W, (float2*)c->X, c->st));
+  } else {
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->X, X0, blk, kind, c->st));
+  }
+  c->iters = c->matvecs = c->restarts = c->last_evals = 0;
+  c->y_fresh = true;
+  c->have_prev = c->converged = false;
+  c->rr_prev = 0.0;
+  c->res0_inf = -1.0;
+  c->last_t = 0.0;
+  c->rel = c->rel_inf = NAN;
+  GSI_TRY(orthonormalize(c));
+  GSI_TRY(op_matvec(c, c->X, c->Y));
+  GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  prof_harvest(c);
+  return GSI_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -322,6 +472,7 @@ gsi_status gsi_default_opts(gsi_opts* o) {
   o->k_restart = 0;
   o->recompute_every = 50;
   o->explicit_ax = 0;
+  o->precision = GSI_PREC_DF64;
   return GSI_OK;
 }
 
@@ -344,6 +495,8 @@ const char* gsi_last_error(void) { return g_last_error; }
 gsi_status gsi_destroy(gsi_ctx* c) {
   if (!c) return GSI_ERR_ARG;
   if (c->st) cudaStreamSynchronize(c->st);
+  prof_harvest(c);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->host) cudaFreeHost(c->host);
   delete c;
@@ -359,7 +512,8 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
   gsi_default_opts(&opts);
   if (o) opts = *o;
   if ((opts.method != GSI_SD && opts.method != GSI_CG) || (opts.which != 1 && opts.which != -1) ||
-      opts.max_iters < 0 || !(opts.tol >= 0.0))
+      opts.max_iters < 0 || !(opts.tol >= 0.0) ||
+      (opts.precision != GSI_PREC_DF64 && opts.precision != GSI_PREC_F64))
     return GSI_ERR_ARG;
   gsi_ctx* c = new gsi_ctx();
   *out = nullptr;
@@ -368,14 +522,15 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
   c->nnz = A->nnz;
   c->p = p;
   c->o = opts;
+  c->emu = opts.precision == GSI_PREC_DF64;
   c->fmt = A->fmt;
   c->sign = opts.which == -1 ? -1.0 : 1.0;
   const int64_t n = c->n;
-  const size_t blk = (size_t)n * p * sizeof(double);
+  const size_t blk = (size_t)n * p * 8;
   gsi_status s = GSI_OK;
-#define CK(expr)               \
-  do {                         \
-    s = (expr);                \
+#define CK(expr)                \
+  do {                          \
+    s = (expr);                 \
     if (s != GSI_OK) goto fail; \
   } while (0)
   {
@@ -390,6 +545,10 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       scale_kernel<<<ceil_div(c->nnz, 256), 256, 0, c->st>>>(c->nnz, -1.0, c->val);
       note_launch();
       CK(cuda_status_ok(cudaGetLastError()));
+    }
+    if (c->emu) {
+      CK(dev_alloc(c, (void**)&c->vdf, c->nnz * sizeof(float2)));
+      CK(df_from_f64(c->nnz, c->val, c->vdf, c->st));
     }
     if (c->fmt == GSI_SELL) {
       c->C = A->sell_C > 0 ? A->sell_C : 32;
@@ -422,23 +581,33 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       CK(cuda_status_ok(cudaMemcpyAsync(c->chunk_len, clen.data(), clen.size() * 8, cudaMemcpyHostToDevice, c->st)));
       CK(cuda_status_ok(cudaMemcpyAsync(c->scol, scol.data(), scol.size() * 4, cudaMemcpyHostToDevice, c->st)));
       CK(cuda_status_ok(cudaMemcpyAsync(c->sval, sval.data(), sval.size() * 8, cudaMemcpyHostToDevice, c->st)));
+      if (c->emu) {
+        CK(dev_alloc(c, (void**)&c->sdf, sval.size() * sizeof(float2)));
+        CK(df_from_f64((int64_t)sval.size(), c->sval, c->sdf, c->st));
+      }
       CK(cuda_status_ok(cudaStreamSynchronize(c->st)));
     }
-    double* bufs[7];
-    for (int i = 0; i < 7; ++i) CK(dev_alloc(c, (void**)&bufs[i], blk));
+    void* bufs[9];
+    for (int i = 0; i < 9; ++i) CK(dev_alloc(c, &bufs[i], blk));
     c->X = bufs[0]; c->Y = bufs[1]; c->R = bufs[2]; c->Rp = bufs[3];
-    c->D = bufs[4]; c->P = bufs[5]; c->W = bufs[6];
+    c->D = bufs[4]; c->P = bufs[5]; c->W = bufs[6]; c->Xn = bufs[7]; c->Yn = bufs[8];
     const size_t q = (size_t)p * p;
     CK(dev_alloc(c, (void**)&c->pp, (8 * q + 64) * sizeof(double)));
     c->Cm = c->pp; c->Bm = c->pp + q; c->Gm = c->pp + 2 * q; c->Zm = c->pp + 3 * q;
     c->XXm = c->pp + 4 * q; c->XDm = c->pp + 5 * q; c->Km = c->pp + 6 * q; c->Mm = c->pp + 7 * q;
     c->out = c->pp + 8 * q;
     c->dout = c->out + 16;
-    CK(dev_alloc(c, (void**)&c->gram_ws, gram_scratch_doubles(n, p, p) * sizeof(double)));
-    CK(dev_alloc(c, (void**)&c->dots_ws, (size_t)dots_blocks(n) * 3 * sizeof(double)));
+    if (c->emu) {
+      CK(dev_alloc(c, (void**)&c->oz_gram_ws, oz_gram_scratch_bytes(n, p, p, false)));
+      CK(dev_alloc(c, &c->oz_rhs_ws, oz_rhs_bytes(p, 2)));
+      CK(dev_alloc(c, (void**)&c->oz_parts, (size_t)oz_gemm_max_parts(p) * 2 * sizeof(float2)));
+      CK(dev_alloc(c, (void**)&c->dots_ws, (size_t)df_dots_blocks(n * p) * 3 * sizeof(float2)));
+    } else {
+      CK(dev_alloc(c, (void**)&c->gram_ws, gram_scratch_doubles(n, p, p) * sizeof(double)));
+      CK(dev_alloc(c, (void**)&c->dots_ws, (size_t)dots_blocks(n) * 3 * sizeof(double)));
+    }
     CK(dev_alloc(c, (void**)&c->small_ws, small_scratch_doubles(p) * sizeof(double)));
     CK(cuda_status_ok(cudaMallocHost((void**)&c->host, std::max<size_t>(q, 64) * sizeof(double))));
-    // anorm
     if (opts.anorm > 0) {
       c->anorm = opts.anorm;
     } else {
@@ -451,12 +620,7 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       c->anorm = c->host[0];
       if (!(c->anorm > 0)) c->anorm = 1.0;
     }
-    CK(cuda_status_ok(cudaMemcpyAsync(c->X, X0, blk,
-                                      X0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                      c->st)));
-    CK(orthonormalize(c));
-    CK(matvec(c, c->X, c->Y));
-    CK(cuda_status_ok(cudaStreamSynchronize(c->st)));
+    CK(start(c, X0, X0_on_device));
   }
 #undef CK
   *out = c;
@@ -464,6 +628,11 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
 fail:
   gsi_destroy(c);
   return s;
+}
+
+gsi_status gsi_reset(gsi_ctx* c, const double* X0, int32_t X0_on_device) {
+  if (!c || !X0) return GSI_ERR_ARG;
+  return start(c, X0, X0_on_device);
 }
 
 gsi_status gsi_step(gsi_ctx* c, int32_t nsteps, gsi_info* info) {
@@ -488,7 +657,7 @@ gsi_status gsi_solve(gsi_ctx* c, gsi_info* info) {
   return c->converged ? GSI_OK : GSI_ERR_NOCONV;
 }
 
-gsi_status gsi_state_ptrs(gsi_ctx* c, double** X, double** Y) {
+gsi_status gsi_state_ptrs(gsi_ctx* c, void** X, void** Y) {
   if (!c) return GSI_ERR_ARG;
   if (X) *X = c->X;
   if (Y) *Y = c->Y;
@@ -498,37 +667,66 @@ gsi_status gsi_state_ptrs(gsi_ctx* c, double** X, double** Y) {
 gsi_status gsi_get_basis(gsi_ctx* c, double* X, double* evals, int32_t to_device) {
   if (!c) return GSI_ERR_ARG;
   const int p = c->p;
-  const size_t blk = (size_t)c->n * p * sizeof(double);
+  const size_t blk = (size_t)blk_bytes(c);
   cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (!evals) {
-    if (X) GSI_CUDA_TRY(cudaMemcpyAsync(X, c->X, blk, kind, c->st));
-    GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
-    return GSI_OK;
+  const void* src = c->X;
+  if (evals) {
+    // Rayleigh-Ritz with an explicit AX: theta in XDm, U in Bm; W and Yn are scratch
+    GSI_TRY(op_matvec(c, c->X, c->W));
+    c->matvecs--;  // not part of the iteration count
+    GSI_TRY(op_gram(c, c->X, c->W, true, c->Km));
+    GSI_TRY(small_eig(p, c->Km, c->XDm, c->Bm, c->small_ws, c->st));
+    if (X) {
+      GSI_TRY(op_blockmul(c, 1, c->X, c->Bm, 1.0, nullptr, nullptr, 0.0, 0, nullptr, 0.0, nullptr,
+                          0.0, c->Yn, false, nullptr));
+      src = c->Yn;
+    }
   }
-  // Rayleigh-Ritz with an explicit AX (W is scratch here): theta in XDm, U in Bm
-  GSI_TRY(spmm_csr(c->n, c->rowptr, c->colidx, c->val, p, c->X, c->W, c->st));
-  GSI_TRY(G(c, c->X, c->W, c->Km));
-  double* U = c->Bm;
-  GSI_TRY(small_eig(p, c->Km, c->XDm, U, c->small_ws, c->st));
   if (X) {
-    RowMulArgs a{};
-    a.nk = 1;
-    a.U[0] = c->X;
-    a.M[0] = U;
-    a.s[0] = 1.0;
-    GSI_TRY(rowmul(c->n, p, a, c->W, c->st));
-    GSI_CUDA_TRY(cudaMemcpyAsync(X, c->W, blk, kind, c->st));
+    if (c->emu) {
+      GSI_TRY(df_to_f64(c->n * p, (const float2*)src, (double*)c->W, c->st));
+      src = c->W;
+    }
+    GSI_CUDA_TRY(cudaMemcpyAsync(X, src, blk, kind, c->st));
   }
-  GSI_CUDA_TRY(cudaMemcpyAsync(c->host, c->XDm, p * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if (evals) {
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->host, c->XDm, p * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  }
   GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
-  std::vector<double> ev(p);
-  for (int i = 0; i < p; ++i) ev[i] = c->sign * c->host[i];
-  if (to_device) {
-    GSI_CUDA_TRY(cudaMemcpy(evals, ev.data(), p * sizeof(double), cudaMemcpyHostToDevice));
-  } else {
-    memcpy(evals, ev.data(), p * sizeof(double));
+  prof_harvest(c);
+  if (evals) {
+    std::vector<double> ev(p);
+    for (int i = 0; i < p; ++i) ev[i] = c->sign * c->host[i];
+    if (to_device) {
+      GSI_CUDA_TRY(cudaMemcpy(evals, ev.data(), p * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+      memcpy(evals, ev.data(), p * sizeof(double));
+    }
   }
   return GSI_OK;
 }
+
+gsi_status gsi_profile_enable(gsi_ctx* c, int32_t on) {
+  if (!c) return GSI_ERR_ARG;
+  GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  prof_harvest(c);
+  c->prof = on != 0;
+  for (auto& k : c->cls) k = gsi_ctx::Cls{};
+  return GSI_OK;
+}
+
+gsi_status gsi_profile_read(gsi_ctx* c, int32_t k, int64_t* launches, double* total_ms,
+                            double* alg_bytes, double* alg_flops) {
+  if (!c || k < 0 || k >= GSI_K_COUNT) return GSI_ERR_ARG;
+  GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  prof_harvest(c);
+  if (launches) *launches = c->cls[k].launches;
+  if (total_ms) *total_ms = c->cls[k].ms;
+  if (alg_bytes) *alg_bytes = c->cls[k].bytes;
+  if (alg_flops) *alg_flops = c->cls[k].flops;
+  return GSI_OK;
+}
+
+int64_t gsi_launch_count(void) { return (int64_t)g_launches.load(); }
 
 }  // extern "C"

@@ -19,12 +19,15 @@ GSI_OK, GSI_ERR_ARG, GSI_ERR_CUDA, GSI_ERR_OOM, GSI_ERR_NOCONV, GSI_ERR_BREAKDOW
     GSI_ERR_NONFINITE, GSI_ERR_TIMEOUT = range(8)
 GSI_CSR, GSI_SELL = 0, 1
 GSI_SD, GSI_CG = 0, 1
+GSI_PREC_DF64, GSI_PREC_F64 = 0, 1
+KERNEL_CLASSES = ["spmm", "gram", "blockmul", "small", "reduce"]
 
 EXPORTED = [
     "gsi_default_opts", "gsi_create", "gsi_step", "gsi_solve", "gsi_get_basis", "gsi_state_ptrs",
     "gsi_destroy", "gsi_status_str", "gsi_last_error", "gsi_spmm_csr", "gsi_sell_size",
     "gsi_csr_to_sell", "gsi_spmm_sell", "gsi_gram", "gsi_residual", "gsi_linesearch",
-    "gsi_retract", "gsi_df_spmm_csr", "gsi_oz_gemm", "gsi_oz_gram",
+    "gsi_retract", "gsi_df_spmm_csr", "gsi_oz_gemm", "gsi_oz_gram", "gsi_reset",
+    "gsi_profile_enable", "gsi_profile_read", "gsi_launch_count",
 ]
 
 
@@ -47,7 +50,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("which", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("anorm", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("k_restart", ctypes.c_int32), ("recompute_every", ctypes.c_int32),
-                ("explicit_ax", ctypes.c_int32)]
+                ("explicit_ax", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -91,6 +94,10 @@ def _lib():
             "gsi_df_spmm_csr": [i64, vp, vp, vp, i32, vp, vp, vp],
             "gsi_oz_gemm": [i64, i32, i32, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp, vp, vp],
             "gsi_oz_gram": [i64, i32, i32, vp, vp, i32, vp, vp],
+            "gsi_reset": [vp, vp, i32],
+            "gsi_profile_enable": [vp, i32],
+            "gsi_profile_read": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
+                                 ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -100,6 +107,8 @@ def _lib():
         L.gsi_status_str.restype = ctypes.c_char_p
         L.gsi_last_error.argtypes = []
         L.gsi_last_error.restype = ctypes.c_char_p
+        L.gsi_launch_count.argtypes = []
+        L.gsi_launch_count.restype = ctypes.c_int64
         _LIB = L
     return _LIB
 
@@ -136,8 +145,8 @@ def _dptr(t, dtype=None, shape=None):
 class _DeviceArray:
     """Zero-copy view of library-owned device memory via __cuda_array_interface__."""
 
-    def __init__(self, ptr, shape):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8",
+    def __init__(self, ptr, shape, typestr="<f8"):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
                                          "data": (int(ptr), False), "version": 3, "strides": None}
 
 
@@ -215,6 +224,11 @@ def retract(t, M, X, D, Y, W, stream=None):
                              _dptr(Y, f, (n, p)), _dptr(W, f, (n, p)), _stream(stream)), "gsi_retract")
 
 
+def launch_count():
+    """Kernels launched by libgsi in this process."""
+    return int(lib().gsi_launch_count())
+
+
 # ----------------------------------------------------------------------------
 # df64 kernels: a df64 tensor is float32 with a trailing dimension of 2 (hi, lo)
 # ----------------------------------------------------------------------------
@@ -279,7 +293,8 @@ class Solver:
     tensors). X0: n x p start block (numpy or torch CUDA float64)."""
 
     def __init__(self, A, p, X0, method="sd", which=1, tol=1e-8, anorm=0.0, max_iters=10000,
-                 k_restart=0, recompute_every=50, explicit_ax=False, fmt="csr", stream=None):
+                 k_restart=0, recompute_every=50, explicit_ax=False, fmt="csr", precision="df64",
+                 stream=None):
         import torch
         L = lib()
         self._keep = []
@@ -304,6 +319,10 @@ class Solver:
         o.k_restart = int(k_restart)
         o.recompute_every = int(recompute_every)
         o.explicit_ax = 1 if explicit_ax else 0
+        if precision not in ("df64", "f64"):
+            raise ValueError("precision must be 'df64' or 'f64'")
+        o.precision = GSI_PREC_DF64 if precision == "df64" else GSI_PREC_F64
+        self.precision = precision
         if isinstance(X0, torch.Tensor):
             x0p, x0dev = _dptr(X0, torch.float64, (A.n, p)), 1
         else:
@@ -348,13 +367,39 @@ class Solver:
         return X, ev
 
     def state(self):
-        """Zero-copy torch views of the current X and Y = AX (library memory)."""
+        """Zero-copy torch views of the current X and Y = AX (library memory):
+        float64 (n, p) for precision 'f64', float32 (n, p, 2) df64 pairs otherwise."""
         import torch
         xp, yp = ctypes.c_void_p(), ctypes.c_void_p()
         _check(lib().gsi_state_ptrs(self._ctx, ctypes.byref(xp), ctypes.byref(yp)), "gsi_state_ptrs")
-        X = torch.as_tensor(_DeviceArray(xp.value, (self.n, self.p)), device="cuda")
-        Y = torch.as_tensor(_DeviceArray(yp.value, (self.n, self.p)), device="cuda")
+        if self.precision == "f64":
+            shape, ts = (self.n, self.p), "<f8"
+        else:
+            shape, ts = (self.n, self.p, 2), "<f4"
+        X = torch.as_tensor(_DeviceArray(xp.value, shape, ts), device="cuda")
+        Y = torch.as_tensor(_DeviceArray(yp.value, shape, ts), device="cuda")
         return X, Y
+
+    def reset(self, X0):
+        import torch
+        if isinstance(X0, torch.Tensor):
+            _check(lib().gsi_reset(self._ctx, _dptr(X0, torch.float64, (self.n, self.p)), 1), "gsi_reset")
+        else:
+            X0 = np.ascontiguousarray(X0, np.float64)
+            _check(lib().gsi_reset(self._ctx, ctypes.c_void_p(X0.ctypes.data), 0), "gsi_reset")
+
+    def profile(self, on=True):
+        _check(lib().gsi_profile_enable(self._ctx, 1 if on else 0), "gsi_profile_enable")
+
+    def profile_read(self):
+        """{class: {launches, ms, bytes, flops}} since profile(True)."""
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            l, ms, b, f = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            _check(lib().gsi_profile_read(self._ctx, k, ctypes.byref(l), ctypes.byref(ms),
+                                          ctypes.byref(b), ctypes.byref(f)), "gsi_profile_read")
+            out[name] = {"launches": l.value, "ms": ms.value, "bytes": b.value, "flops": f.value}
+        return out
 
     def close(self):
         if getattr(self, "_ctx", None):

@@ -209,8 +209,9 @@ def _trajectory_oracle(S, X0, opts, k):
     return traj
 
 
+@pytest.mark.parametrize("precision", ["df64", "f64"])
 @pytest.mark.parametrize("method", ["sd", "cg"])
-def test_trajectory_matches_oracle(torch_cuda, method):
+def test_trajectory_matches_oracle(torch_cuda, method, precision):
     """First 10 iterations of the 2D 32 x 32 problem, p = 8: X_k and t_k agree."""
     from paper_2306_10379_gb300 import gsi
     dims, p = (32, 32), 8
@@ -220,7 +221,7 @@ def test_trajectory_matches_oracle(torch_cuda, method):
     X0 = I.start_block(A.n, p, I.SEED_BASE)
     opts = O.Options(method=method, tol=1e-8, anorm=lam[0])
     ref = _trajectory_oracle(S, X0, opts, 10)
-    with gsi.Solver(A, p, X0, method=method, tol=1e-8, anorm=lam[0]) as s:
+    with gsi.Solver(A, p, X0, method=method, tol=1e-8, anorm=lam[0], precision=precision) as s:
         for k in range(10):
             info = s.step(1)
             X, _ = s.basis(evals=False)
@@ -229,8 +230,10 @@ def test_trajectory_matches_oracle(torch_cuda, method):
             assert np.max(np.abs(X - Xr)) <= 1e-10, k
 
 
-@pytest.mark.parametrize("method,fmt", [("sd", "csr"), ("cg", "csr"), ("cg", "sell")])
-def test_converges_2d_closed_form(torch_cuda, method, fmt):
+@pytest.mark.parametrize("method,fmt,precision", [("sd", "csr", "df64"), ("cg", "csr", "df64"),
+                                                  ("cg", "sell", "df64"), ("sd", "csr", "f64"),
+                                                  ("cg", "sell", "f64")])
+def test_converges_2d_closed_form(torch_cuda, method, fmt, precision):
     """2D 5-point Laplacian 32 x 32, p = 8: relative residual 1e-8 and Ritz values
     4 sin^2(i pi/66) + 4 sin^2(j pi/66); the subspace is within the Davis-Kahan
     bound of the exact one; X^T X = I."""
@@ -240,7 +243,7 @@ def test_converges_2d_closed_form(torch_cuda, method, fmt):
     S = O.csr_operator(A.n, A.rowptr, A.colidx, A.val).toarray()
     lam = I.laplacian_eigenvalues(dims)
     with gsi.Solver(A, p, I.start_block(A.n, p, I.SEED_BASE), method=method, tol=1e-8,
-                    anorm=lam[0], fmt=fmt) as s:
+                    anorm=lam[0], fmt=fmt, precision=precision) as s:
         info = s.solve()
         X, ev = s.basis()
     assert info["converged"] == 1 and info["rel_residual"] <= 1e-8
@@ -258,14 +261,15 @@ def test_converges_2d_closed_form(torch_cuda, method, fmt):
     assert abs(info["iters"] - ores.iters) <= max(2, 0.02 * ores.iters)
 
 
-def test_min_problem(torch_cuda):
+@pytest.mark.parametrize("precision", ["df64", "f64"])
+def test_min_problem(torch_cuda, precision):
     """which = -1 runs on -A and returns the smallest eigenvalues (Sec. 2.1)."""
     from paper_2306_10379_gb300 import gsi
     dims, p = (14, 13), 4
     A = I.fd_laplacian(dims)
     lam = I.laplacian_eigenvalues(dims)
     with gsi.Solver(A, p, I.start_block(A.n, p, 2), method="cg", which=-1, tol=1e-9,
-                    anorm=lam[0]) as s:
+                    anorm=lam[0], precision=precision) as s:
         info = s.solve()
         X, ev = s.basis()
     assert info["converged"] == 1
@@ -291,3 +295,41 @@ def test_nonconvergence_status(torch_cuda):
         with pytest.raises(gsi.GsiError) as e:
             s.solve(raise_on_noconv=True)
         assert e.value.status == gsi.GSI_ERR_NOCONV
+
+
+@pytest.mark.parametrize("p", [1, 6, 100])
+def test_df64_solver_odd_sizes(torch_cuda, p):
+    """Whole method in df64 with p outside the 16-multiple tile grid and p > 64
+    (two output column slices): converges to the closed-form spectrum."""
+    from paper_2306_10379_gb300 import gsi
+    dims = (20, 19, 3) if p <= 6 else (30, 29)
+    A = I.fd_laplacian(dims)
+    lam = I.laplacian_eigenvalues(dims)
+    gap = lam[p - 1] - lam[p]
+    assert gap > 1e-6
+    with gsi.Solver(A, p, I.start_block(A.n, p, 4), method="cg", tol=1e-9, anorm=lam[0],
+                    max_iters=5000) as s:
+        info = s.solve()
+        X, ev = s.basis()
+    assert info["converged"] == 1
+    assert np.max(np.abs(ev - lam[:p])) <= 1e-12 * lam[0] + 2 * (1e-9 * lam[0]) ** 2 / gap * 10
+    assert np.max(np.abs(X.T @ X - np.eye(p))) < 1e-12
+
+
+def test_reset_and_profile(torch_cuda):
+    from paper_2306_10379_gb300 import gsi
+    dims, p = (24, 24), 8
+    A = I.fd_laplacian(dims)
+    lam = I.laplacian_eigenvalues(dims)
+    X0 = I.start_block(A.n, p, 1)
+    with gsi.Solver(A, p, X0, method="cg", tol=1e-8, anorm=lam[0]) as s:
+        i1 = s.solve()
+        s.profile(True)
+        s.reset(X0)
+        n0 = gsi.launch_count()
+        i2 = s.solve()
+        prof = s.profile_read()
+        assert gsi.launch_count() > n0
+    assert i1["iters"] == i2["iters"] and i1["rel_residual"] == i2["rel_residual"]
+    assert prof["spmm"]["launches"] == i2["matvecs"]  # includes the start-block matvec of reset
+    assert all(prof[k]["ms"] > 0 for k in ("spmm", "gram", "blockmul", "small"))
