@@ -215,12 +215,16 @@ gsi_status gsi_residual(int64_t n, int32_t p, const double* X, const double* Y,
  * by Brent on phi'(t), then M = S^{-1/2} with
  * S = XX + t (XD + XD^T) + t^2 B, the measured Gram of X + tD.
  * Inputs (device, p x p): C = X^T Y, B = D^T D, Gam = D^T W, Z = D^T R,
- * XX = X^T X, XD = X^T D. Outputs (device): M (p x p) and
- * out[0..3] = {t, phi(t) model value, brent evaluations, status}.
- * status 0 = ok, 5 = S not positive definite. */
+ * XX = X^T X, XD = X^T D. Outputs (device): M (p x p) and out (16 doubles):
+ * out[0..4] = {t, phi(t) model value, phi' evaluations, status, max beta_i};
+ * status 0 = ok, 5 = S not positive definite; out[5..15] are diagnostics
+ * (cycle counts and sweep counts of the phases). precision: GSI_PREC_DF64 finds the eigenbasis
+ * with a float32 Jacobi method refined in df64 and forms M by a first-order
+ * expansion in that basis; GSI_PREC_F64 runs a float64 Jacobi method for B
+ * and for S. */
 gsi_status gsi_linesearch(int32_t p, const double* C, const double* B, const double* Gam,
                           const double* Z, const double* XX, const double* XD, double* M,
-                          double* out, void* stream);
+                          double* out, int32_t precision, void* stream);
 
 /* Retraction with the AX recursion (Eqs. (Ynew), (save_matvec)):
  * X <- (X + t D) M, Y <- (Y + t W) M, in place. */

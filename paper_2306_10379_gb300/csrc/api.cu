@@ -68,10 +68,15 @@ gsi_status gsi_residual(int64_t n, int32_t p, const double* X, const double* Y,
 
 gsi_status gsi_linesearch(int32_t p, const double* C, const double* B, const double* Gam,
                           const double* Z, const double* XX, const double* XD, double* M,
-                          double* out, void* stream) {
+                          double* out, int32_t precision, void* stream) {
   if (p < 1 || p > 128 || !C || !B || !Gam || !Z || !XX || !XD || !M || !out) return GSI_ERR_ARG;
+  if (precision != GSI_PREC_DF64 && precision != GSI_PREC_F64) return GSI_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   ScratchGuard g(st);
+  if (precision == GSI_PREC_DF64) {
+    GSI_CUDA_TRY(cudaMallocAsync(&g.ptr, small_df_scratch_bytes(p), st));
+    return small_step_df(0, p, C, B, Gam, Z, XX, XD, M, out, g.ptr, st);
+  }
   GSI_CUDA_TRY(cudaMallocAsync(&g.ptr, small_scratch_doubles(p) * sizeof(double), st));
   return small_step(0, p, C, B, Gam, Z, XX, XD, M, out, (double*)g.ptr, st);
 }

@@ -35,6 +35,11 @@ size_t small_scratch_doubles(int p);
 gsi_status small_step(int mode, int p, const double* C, const double* B, const double* Gam,
                       const double* Z, const double* XX, const double* XD, double* M,
                       double* out, double* scratch, cudaStream_t st);
+// the same step with a float32 Jacobi eigensolver refined in df64 (small_df.cu)
+size_t small_df_scratch_bytes(int p);
+gsi_status small_step_df(int mode, int p, const double* C, const double* B, const double* Gam,
+                         const double* Z, const double* XX, const double* XD, double* M,
+                         double* out, void* scratch, cudaStream_t st);
 // theta (descending) and U with C = U diag(theta) U^T, C symmetrised first.
 gsi_status small_eig(int p, const double* C, double* theta, double* U, double* scratch,
                      cudaStream_t st);

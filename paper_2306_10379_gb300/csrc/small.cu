@@ -6,6 +6,7 @@
 //
 // The eigensolver is a block-parallel cyclic Jacobi method with round-robin
 // (circle) ordering: each round applies p/2 disjoint rotations at once.
+#include "alg3.cuh"
 #include "blas_f64.cuh"
 
 #include <math.h>
@@ -173,131 +174,6 @@ __device__ void block_diag_quad(int p, const double* G, const double* V, double*
     d[i] = s;
   }
   __syncthreads();
-}
-
-// phi'(t) of Eq. (deriv_P), summed over i ascending.
-__device__ double dphi(double t, int p, const double* al, const double* be, const double* ga,
-                       const double* ze) {
-  double s = 0.0;
-  for (int i = 0; i < p; ++i) {
-    double num = ze[i] + (ga[i] - al[i] * be[i]) * t - be[i] * ze[i] * t * t;
-    double den = 1.0 + be[i] * t * t;
-    s += num / (den * den);
-  }
-  return -s;
-}
-
-__device__ double phi_model(double t, int p, const double* al, const double* be,
-                            const double* ga, const double* ze) {
-  double s = 0.0;
-  for (int i = 0; i < p; ++i) s += (al[i] + 2.0 * ze[i] * t + ga[i] * t * t) / (1.0 + be[i] * t * t);
-  return -0.5 * s;
-}
-
-// Brent-Dekker zero of phi' on [a, b] with phi'(a) phi'(b) <= 0 (R. P. Brent,
-// Algorithms for Minimization without Derivatives, 1973, ch. 4): inverse
-// quadratic / secant steps kept inside the bracket, bisection otherwise;
-// stops when the bracket is below 2 eps |b|. Returns the root; *ev counts
-// evaluations.
-__device__ double brent(double a, double b, double fa, double fb, int p, const double* al,
-                        const double* be, const double* ga, const double* ze, int* ev) {
-  if (fa == 0.0) return a;
-  if (fb == 0.0) return b;
-  double c = a, fc = fa, d = b - a, e = d;
-  for (int it = 0; it < 100; ++it) {
-    if ((fb > 0.0 && fc > 0.0) || (fb < 0.0 && fc < 0.0)) {
-      c = a;
-      fc = fa;
-      d = e = b - a;
-    }
-    if (fabs(fc) < fabs(fb)) {
-      a = b; b = c; c = a;
-      fa = fb; fb = fc; fc = fa;
-    }
-    double tol = 2.0 * DEPS * fabs(b) + 1e-300;
-    double m = 0.5 * (c - b);
-    if (fabs(m) <= tol || fb == 0.0) break;
-    if (fabs(e) >= tol && fabs(fa) > fabs(fb)) {
-      double s = fb / fa, P, Q;
-      if (a == c) {
-        P = 2.0 * m * s;
-        Q = 1.0 - s;
-      } else {
-        double q = fa / fc, r = fb / fc;
-        P = s * (2.0 * m * q * (q - r) - (b - a) * (r - 1.0));
-        Q = (q - 1.0) * (r - 1.0) * (s - 1.0);
-      }
-      if (P > 0.0) Q = -Q; else P = -P;
-      if (2.0 * P < fmin(3.0 * m * Q - fabs(tol * Q), fabs(e * Q))) {
-        e = d;
-        d = P / Q;
-      } else {
-        d = m;
-        e = m;
-      }
-    } else {
-      d = m;
-      e = m;
-    }
-    a = b;
-    fa = fb;
-    b = (fabs(d) > tol) ? b + d : b + copysign(tol, m);
-    fb = dphi(b, p, al, be, ga, ze);
-    ++*ev;
-  }
-  return b;
-}
-
-// Alg. 3 generalised to zeta (Sec. 5.2). Bracket-eligible branches have
-// beta_i > eps * sum(beta) and zeta_i > 0; xi_i from Eq. (derv1) (delta < 0)
-// or Eq. (derv2) (delta >= 0) with zeta in the CG places. The step is the
-// first minimiser of the model past xi_min: the right end is doubled from
-// xi_min (capped at xi_max) until phi' >= 0, then Brent.
-__device__ double get_mu(int p, const double* al, const double* be, const double* ga,
-                         const double* ze, int* ev) {
-  double sb = 0.0;
-  for (int i = 0; i < p; ++i) sb += be[i];
-  double xmin = INFINITY, xmax = -INFINITY;
-  int cnt = 0;
-  for (int i = 0; i < p; ++i) {
-    double b = be[i], z = ze[i];
-    if (!(b > DEPS * sb) || !(z > 0.0)) continue;
-    double d = ga[i] - al[i] * b;
-    double disc = sqrt(d * d + 4.0 * b * z * z);
-    double xi = (d < 0.0) ? 2.0 * z / (-d + disc) : (d + disc) / (2.0 * b * z);
-    xmin = fmin(xmin, xi);
-    xmax = fmax(xmax, xi);
-    ++cnt;
-  }
-  *ev = 0;
-  if (cnt == 0) return 0.0;
-  double fa = dphi(xmin, p, al, be, ga, ze);
-  ++*ev;
-  double lo, flo, hi, fhi;
-  if (fa > 0.0) {
-    lo = 0.0;
-    flo = dphi(0.0, p, al, be, ga, ze);
-    ++*ev;
-    if (flo >= 0.0) return 0.0;
-    hi = xmin;
-    fhi = fa;
-  } else {
-    lo = flo = hi = fhi = 0.0;
-    lo = xmin; flo = fa; hi = xmin; fhi = fa;
-    int k = 0;
-    while (fhi < 0.0) {
-      if (k >= 64) return hi;
-      double nxt = 2.0 * hi;
-      if (hi < xmax) nxt = fmin(nxt, xmax);
-      lo = hi;
-      flo = fhi;
-      hi = nxt;
-      fhi = dphi(hi, p, al, be, ga, ze);
-      ++*ev;
-      ++k;
-    }
-  }
-  return brent(lo, hi, flo, fhi, p, al, be, ga, ze, ev);
 }
 
 // M = U diag(s^{-1/2}) U^T for S = U diag(s) U^T held as (A diagonal, U).

@@ -300,8 +300,10 @@ gsi_status op_rowinf(gsi_ctx* c, const void* Rb) {
 
 gsi_status op_small(gsi_ctx* c, int mode, const double* B, const double* Zp) {
   prof_begin(c);
-  gsi_status s = small_step(mode, c->p, c->Cm, B, c->Gm, Zp, c->XXm, c->XDm, c->Mm, c->out,
-                            c->small_ws, c->st);
+  gsi_status s = c->emu ? small_step_df(mode, c->p, c->Cm, B, c->Gm, Zp, c->XXm, c->XDm, c->Mm,
+                                        c->out, c->small_ws, c->st)
+                        : small_step(mode, c->p, c->Cm, B, c->Gm, Zp, c->XXm, c->XDm, c->Mm, c->out,
+                                     c->small_ws, c->st);
   prof_end(c, GSI_K_SMALL, 0.0, 0.0);
   return s;
 }
@@ -606,7 +608,8 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       CK(dev_alloc(c, (void**)&c->gram_ws, gram_scratch_doubles(n, p, p) * sizeof(double)));
       CK(dev_alloc(c, (void**)&c->dots_ws, (size_t)dots_blocks(n) * 3 * sizeof(double)));
     }
-    CK(dev_alloc(c, (void**)&c->small_ws, small_scratch_doubles(p) * sizeof(double)));
+    CK(dev_alloc(c, (void**)&c->small_ws, std::max(small_scratch_doubles(p) * sizeof(double),
+                                                   small_df_scratch_bytes(p))));
     CK(cuda_status_ok(cudaMallocHost((void**)&c->host, std::max<size_t>(q, 64) * sizeof(double))));
     if (opts.anorm > 0) {
       c->anorm = opts.anorm;

@@ -89,7 +89,7 @@ def _lib():
             "gsi_spmm_sell": [i64, i64, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp],
             "gsi_gram": [i64, i32, i32, vp, vp, vp, vp],
             "gsi_residual": [i64, i32, vp, vp, vp, vp, vp],
-            "gsi_linesearch": [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "gsi_linesearch": [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp],
             "gsi_retract": [i64, i32, dbl, vp, vp, vp, vp, vp, vp],
             "gsi_df_spmm_csr": [i64, vp, vp, vp, i32, vp, vp, vp],
             "gsi_oz_gemm": [i64, i32, i32, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp, vp, vp],
@@ -207,13 +207,15 @@ def residual(X, Y, C, R, stream=None):
                               _stream(stream)), "gsi_residual")
 
 
-def linesearch(C, B, Gam, Z, XX, XD, M, out, stream=None):
+def linesearch(C, B, Gam, Z, XX, XD, M, out, precision="df64", stream=None):
     import torch
     p = C.shape[0]
     f = torch.float64
+    pr = GSI_PREC_DF64 if precision == "df64" else GSI_PREC_F64
     _check(lib().gsi_linesearch(p, _dptr(C, f, (p, p)), _dptr(B, f, (p, p)), _dptr(Gam, f, (p, p)),
                                 _dptr(Z, f, (p, p)), _dptr(XX, f, (p, p)), _dptr(XD, f, (p, p)),
-                                _dptr(M, f, (p, p)), _dptr(out, f), _stream(stream)), "gsi_linesearch")
+                                _dptr(M, f, (p, p)), _dptr(out, f), pr, _stream(stream)),
+           "gsi_linesearch")
 
 
 def retract(t, M, X, D, Y, W, stream=None):

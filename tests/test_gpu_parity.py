@@ -159,13 +159,15 @@ def test_residual(torch_cuda, p):
     assert np.all(np.abs(out.cpu().numpy() - R) <= TOL * bound)
 
 
-@pytest.mark.parametrize("cg,p", [(False, 1), (False, 6), (True, 6), (False, 32), (True, 64)])
-def test_linesearch(torch_cuda, cg, p):
+@pytest.mark.parametrize("precision", ["df64", "f64"])
+@pytest.mark.parametrize("cg,p", [(False, 1), (False, 6), (True, 6), (True, 7), (False, 32), (True, 64),
+                                  (True, 100), (False, 128)])
+def test_linesearch(torch_cuda, cg, p, precision):
     """Alg. 3 + polar factor: t within 1e-12 (relative), phi(t) within 1e-13,
     M within 1e-12 of the oracle's (Z^T Z)^{-1/2}."""
     torch = torch_cuda
     from paper_2306_10379_gb300 import gsi
-    dims = (24, 20) if p <= 32 else (30, 30)
+    dims = (24, 20) if p <= 32 else (30, 30) if p <= 64 else (40, 40)
     S, X, Y, C, R, D, W = _state(dims=dims, p=p, cg=cg)
     B, Gam, Z = O.gram(D, D), O.gram(D, W), (O.gram(D, R) if cg else O.gram(D, D))
     XX, XD = O.gram(X, X), O.gram(X, D)
@@ -174,17 +176,19 @@ def test_linesearch(torch_cuda, cg, p):
     Zt = X + t_ref * D
     M_ref = O.inverse_sqrt(O.gram(Zt, Zt))
     M = torch.empty((p, p), dtype=torch.float64, device="cuda")
-    out = torch.zeros(8, dtype=torch.float64, device="cuda")
-    gsi.linesearch(*(_dev(torch, m) for m in (C, B, Gam, Z, XX, XD)), M, out)
+    out = torch.zeros(16, dtype=torch.float64, device="cuda")
+    gsi.linesearch(*(_dev(torch, m) for m in (C, B, Gam, Z, XX, XD)), M, out, precision=precision)
     o = out.cpu().numpy()
     assert o[3] == 0.0
     t = o[0]
-    assert abs(t - t_ref) <= 1e-12 * t_ref
+    # t is a root of phi'; df64 coefficients move it by ~1e-12 relative, which
+    # changes phi(t) only at second order (checked at 1e-13 below)
+    assert abs(t - t_ref) <= (1e-12 if precision == "f64" else 1e-10) * t_ref
     phi_ref = O.phi_model(t_ref, a, b, g, z)
     assert abs(O.phi_model(t, a, b, g, z) - phi_ref) <= 1e-13 * abs(phi_ref)
-    assert abs(o[1] - phi_ref) <= 1e-13 * abs(phi_ref)
+    assert abs(o[1] - phi_ref) <= (1e-13 if precision == "f64" else 1e-12) * abs(phi_ref)
     assert _rel(M.cpu().numpy(), M_ref) <= TOL
-    assert abs(o[4] - b.max()) <= 1e-12 * b.max()
+    assert abs(o[4] - b.max()) <= (1e-12 if precision == "f64" else 1e-10) * b.max()
 
 
 def test_retract(torch_cuda):
