@@ -331,4 +331,42 @@ gsi_status dots(int64_t n, int p, int ndots, const double* A0, const double* B0,
   return GSI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// p x p float64 helpers spread over many blocks (one thread per output):
+//   out = alpha * A B + beta * E      (pp_gemm; E may be null)
+//   out = a * X + b * Y               (pp_axpby)
+// ---------------------------------------------------------------------------
+__global__ void pp_gemm_kernel(int p, double alpha, const double* A, const double* B, double beta,
+                               const double* E, double* out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p * p) return;
+  int i = e / p, j = e - i * p;
+  double s = 0.0;
+  for (int k = 0; k < p; ++k) s = fma(A[i * p + k], B[k * p + j], s);
+  double v = alpha * s;
+  if (E) v = fma(beta, E[e], v);
+  out[e] = v;
+}
+
+__global__ void pp_axpby_kernel(int p, double a, const double* X, double b, const double* Y,
+                                double* out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p * p) return;
+  out[e] = a * X[e] + (Y ? b * Y[e] : 0.0);
+}
+
+gsi_status pp_gemm(int p, double alpha, const double* A, const double* B, double beta,
+                   const double* E, double* out, cudaStream_t st) {
+  pp_gemm_kernel<<<ceil_div(p * p, 64), 64, 0, st>>>(p, alpha, A, B, beta, E, out);
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
+gsi_status pp_axpby(int p, double a, const double* X, double b, const double* Y, double* out,
+                    cudaStream_t st) {
+  pp_axpby_kernel<<<ceil_div(p * p, 256), 256, 0, st>>>(p, a, X, b, Y, out);
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
 }  // namespace gsi

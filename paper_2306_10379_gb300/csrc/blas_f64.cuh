@@ -28,6 +28,12 @@ gsi_status dots(int64_t n, int p, int ndots, const double* A0, const double* B0,
                 const double* A1, const double* B1, const double* Rnorm, double* out,
                 double* scratch, cudaStream_t st);
 
+// p x p float64 products over many blocks: out = alpha A B + beta E; out = a X + b Y
+gsi_status pp_gemm(int p, double alpha, const double* A, const double* B, double beta,
+                   const double* E, double* out, cudaStream_t st);
+gsi_status pp_axpby(int p, double a, const double* X, double b, const double* Y, double* out,
+                    cudaStream_t st);
+
 // p x p step (small.cu)
 size_t small_scratch_doubles(int p);
 // mode 0: line search + polar factor (see gsi_linesearch); mode 1: M = S^{-1/2}

@@ -5,13 +5,17 @@
 // One iteration (R = AX - XC is the residual, -grad phi; the step is
 // X + tD with t >= 0):
 //   C = X^T Y; R = Y - X C; stop if ||R||_F <= tol * anorm (explicit AX)
-//   D = R (SD), or D = R + b (P - X (X^T P)) with the Polak-Ribiere b (CG,
-//       restart to R when <D, R> <= 0 or every k_restart iterations)
+//   D = R (SD), or D = R + b (P - X K), K = X^T P, with the Polak-Ribiere b
+//       (CG, restart to R when <D, R> <= 0 or every k_restart iterations)
 //   W = A D
-//   B = D^T D, Gam = D^T W, Z = D^T R (SD: Z = B), XX = X^T X, XD = X^T D
+//   B = D^T D, Gam = D^T W, Z = D^T R (SD: Z = B), XX = X^T X
+//   XD = X^T D = (I - XX)(C + b K)   (closed form, see below)
 //   (t, M) from the p x p step; X <- (X + tD) M, Y <- (Y + tW) M
-// where M = S^{-1/2} with S = XX + t (XD + XD^T) + t^2 B, the measured Gram
-// of X + tD, so that (X + tD) M is its polar factor (Eq. (Ynew)).
+//   K_next = X_new^T D = M (XD + t B)  (CG, closed form)
+// where M = S^{-1/2} with S = XX + t (XD + XD^T) + t^2 B, the Gram of X + tD,
+// so that (X + tD) M is its polar factor (Eq. (Ynew)). S carries the measured
+// departure of X from orthonormality (XX) and the tangency error it causes
+// (XD), which keeps ||X^T X - I|| at rounding level.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -111,7 +115,7 @@ struct gsi_ctx {
   void *X = nullptr, *Y = nullptr, *R = nullptr, *Rp = nullptr, *D = nullptr, *P = nullptr,
        *W = nullptr, *Xn = nullptr, *Yn = nullptr;
   double* pp = nullptr;  // p x p matrices
-  double *Cm, *Bm, *Gm, *Zm, *XXm, *XDm, *Km, *Mm, *out, *dout;
+  double *Cm, *Bm, *Gm, *Zm, *XXm, *XDm, *Km, *Mm, *Gm2, *out, *dout;
   double* gram_ws = nullptr;
   float2* oz_gram_ws = nullptr;
   void* oz_rhs_ws = nullptr;
@@ -358,10 +362,11 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
   // search direction
   const void* Dp = c->R;
   bool restarted = false;
+  double beta_used = 0.0;
   if (cg) {
     if (c->have_prev) {
       double b = (rr - rp) / c->rr_prev;
-      GSI_TRY(op_gram(c, c->X, c->P, false, c->Km));
+      // K = X^T P was carried over from the previous step in closed form
       // D = R + b P - X (b K), with <D, R>
       GSI_TRY(op_blockmul(c, 1, c->X, c->Km, -b, nullptr, nullptr, 0.0, 2, c->R, 1.0, c->P, b,
                           c->D, false, c->R));
@@ -374,6 +379,7 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
     }
     if (restarted) c->restarts++;
     Dp = c->D;
+    beta_used = (c->have_prev && !restarted) ? (rr - rp) / c->rr_prev : 0.0;
   }
   GSI_TRY(op_matvec(c, Dp, c->W));
   GSI_TRY(op_gram(c, Dp, Dp, true, c->Bm));
@@ -384,7 +390,12 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
     Zp = c->Zm;
   }
   GSI_TRY(op_gram(c, c->X, c->X, true, c->XXm));
-  GSI_TRY(op_gram(c, c->X, Dp, false, c->XDm));
+  // X^T D in closed form from the measured X^T X: X^T R = (I - X^T X) C and
+  // X^T P = K give X^T D = (I - X^T X)(C + b K) (b = 0 for SD and restarts)
+  prof_begin(c);
+  GSI_TRY(pp_axpby(c->p, 1.0, c->Cm, beta_used, beta_used != 0.0 ? c->Km : nullptr, c->Gm2, c->st));
+  GSI_TRY(pp_gemm(c->p, -1.0, c->XXm, c->Gm2, 1.0, c->Gm2, c->XDm, c->st));
+  prof_end(c, GSI_K_SMALL, 0.0, 0.0);
   GSI_TRY(op_small(c, 0, c->Bm, Zp));
   GSI_TRY(readback(c, c->out, 5));
   const double t = c->host[0];
@@ -393,6 +404,13 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
   if (c->host[3] != 0.0) return GSI_ERR_BREAKDOWN;
   if (!isfinite(t)) return GSI_ERR_NONFINITE;
   const double bmax = c->host[4];
+  if (cg) {
+    // next step's K = X_new^T D = M (X^T D + t D^T D)
+    prof_begin(c);
+    GSI_TRY(pp_axpby(c->p, 1.0, c->XDm, t, c->Bm, c->Gm2, c->st));
+    GSI_TRY(pp_gemm(c->p, 1.0, c->Mm, c->Gm2, 0.0, nullptr, c->Km, c->st));
+    prof_end(c, GSI_K_SMALL, 0.0, 0.0);
+  }
   bool recompute = c->o.explicit_ax || t * sqrt(std::max(bmax, 0.0)) < 1e3 * 2.220446049250313e-16 ||
                    (c->o.recompute_every > 0 && (c->iters + 1) % c->o.recompute_every == 0);
   // X <- (X + tD) M, Y <- (Y + tW) M (Eq. (save_matvec)) or Y <- A X
@@ -594,10 +612,11 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
     c->X = bufs[0]; c->Y = bufs[1]; c->R = bufs[2]; c->Rp = bufs[3];
     c->D = bufs[4]; c->P = bufs[5]; c->W = bufs[6]; c->Xn = bufs[7]; c->Yn = bufs[8];
     const size_t q = (size_t)p * p;
-    CK(dev_alloc(c, (void**)&c->pp, (8 * q + 64) * sizeof(double)));
+    CK(dev_alloc(c, (void**)&c->pp, (9 * q + 64) * sizeof(double)));
     c->Cm = c->pp; c->Bm = c->pp + q; c->Gm = c->pp + 2 * q; c->Zm = c->pp + 3 * q;
     c->XXm = c->pp + 4 * q; c->XDm = c->pp + 5 * q; c->Km = c->pp + 6 * q; c->Mm = c->pp + 7 * q;
-    c->out = c->pp + 8 * q;
+    c->Gm2 = c->pp + 8 * q;
+    c->out = c->pp + 9 * q;
     c->dout = c->out + 16;
     if (c->emu) {
       CK(dev_alloc(c, (void**)&c->oz_gram_ws, oz_gram_scratch_bytes(n, p, p, false)));

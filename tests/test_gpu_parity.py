@@ -254,7 +254,8 @@ def test_converges_2d_closed_form(torch_cuda, method, fmt, precision):
     assert np.max(np.abs(ev - lam[:p]) / lam[:p]) < 1e-10
     R = S @ X - X * ev
     assert np.linalg.norm(R) / lam[0] <= 1.01e-8
-    assert np.max(np.abs(X.T @ X - np.eye(p))) < 1e-13
+    # df64 block products round at ~2^-45
+    assert np.max(np.abs(X.T @ X - np.eye(p))) < (1e-13 if precision == "f64" else 5e-13)
     w, U = np.linalg.eigh(S)
     Uex = U[:, ::-1][:, :p]
     ang = O.principal_angles(X, Uex).max()
