@@ -147,10 +147,22 @@ __global__ void oz_prep_rhs_kernel(int p, int p16, int nk, int K16, const double
   }
 }
 
+// cp.async staging (8-byte granularity, zero fill for out-of-range elements)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
-// oz_gemm: rows in tiles of RT = 32, output columns in slices of up to 64
-// (blockIdx.y). 8 warps: 2 row groups of 16 x 4 column groups; each warp owns
-// up to 2 n-tiles of 8 columns.
+// oz_gemm: OUT = (U0 + a1 U1) M + sum_e c_e E_e, M already scaled and cut
+// into digits (oz_prep_rhs). Rows in tiles of RT = 32, output columns in
+// slices of up to 64 (blockIdx.y). 8 warps: 2 row groups of 16 x 4 column
+// groups; each warp owns up to 2 n-tiles of 8 columns. The raw df64 rows of
+// the next tile are fetched with cp.async while the current tile is on the
+// tensor cores.
 // ---------------------------------------------------------------------------
 constexpr int GM_RT = 32;
 constexpr int GM_THREADS = 256;
@@ -158,23 +170,40 @@ constexpr int GM_THREADS = 256;
 __host__ __device__ inline int gm_ud_stride(int K16) { return K16 + 8; }   // bf16 elements per row
 __host__ __device__ inline int gm_md_stride(int K16) { return K16 + 8; }
 
-size_t oz_gemm_smem(int K16, int NC) {
+size_t oz_gemm_smem(int K16, int NC, int nraw) {
   return (size_t)ND * GM_RT * gm_ud_stride(K16) * 2 + (size_t)ND * NC * gm_md_stride(K16) * 2 +
-         (GM_RT + NC) * sizeof(int);
+         (size_t)nraw * GM_RT * K16 * sizeof(float2) + (GM_RT + NC) * sizeof(int) + 64;
 }
 
-__global__ void __launch_bounds__(GM_THREADS)
-oz_gemm_kernel(int64_t n, int p, int p16, int nk, int K16, OzGemmArgs a) {
+__device__ __forceinline__ void gm_stage(const OzGemmArgs& a, int64_t n, int p, int K16, int64_t r0,
+                                         float2* raw0, float2* raw1) {
+  for (int e = threadIdx.x; e < GM_RT * K16; e += GM_THREADS) {
+    int rr = e / K16, k = e - rr * K16;
+    int64_t R = r0 + rr;
+    bool ok = R < n && k < p;
+    int64_t idx = ok ? R * p + k : 0;
+    cp_async8(raw0 + e, a.U[0] + idx, ok);
+    if (raw1) cp_async8(raw1 + e, a.U[1] + idx, ok);
+  }
+  cp_async_commit();
+}
+
+__global__ void __launch_bounds__(GM_THREADS, 2)
+oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int col0 = blockIdx.y * 64;
   const int NC = min(64, p16 - col0);
   const int uds = gm_ud_stride(K16), mds = gm_md_stride(K16);
+  const bool two = a.fuse_u1 != 0;
   __nv_bfloat16* Ud = reinterpret_cast<__nv_bfloat16*>(smem);
   __nv_bfloat16* Ms = Ud + (size_t)ND * GM_RT * uds;
-  int* Er = reinterpret_cast<int*>(Ms + (size_t)ND * NC * mds);
+  float2* raw0 = reinterpret_cast<float2*>(Ms + (size_t)ND * NC * mds);
+  float2* raw1 = two ? raw0 + GM_RT * K16 : nullptr;
+  int* Er = reinterpret_cast<int*>(raw0 + (two ? 2 : 1) * GM_RT * K16);
   int* Fs = Er + GM_RT;
-  const int K = nk * p;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t ntiles = (n + GM_RT - 1) / GM_RT;
+  if ((int64_t)blockIdx.x < ntiles) gm_stage(a, n, p, K16, (int64_t)blockIdx.x * GM_RT, raw0, raw1);
 
   // right operand digits for this column slice
   for (int e = tid; e < ND * NC * (K16 / 8); e += GM_THREADS) {
@@ -187,50 +216,41 @@ oz_gemm_kernel(int64_t n, int p, int p16, int nk, int K16, OzGemmArgs a) {
   for (int e = tid; e < NC; e += GM_THREADS) Fs[e] = a.F[col0 + e];
 
   float2 dacc0 = make_float2(0.f, 0.f), dacc1 = make_float2(0.f, 0.f);
-  const int64_t ntiles = (n + GM_RT - 1) / GM_RT;
   const int wr = warp >> 2, wc = warp & 3;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * GM_RT;
-    __syncthreads();  // previous tile's readers are done with Ud / Er
-    // (a) row exponents over the K columns of [U_0 U_1]
+    cp_async_wait_all();
+    __syncthreads();  // raw rows of this tile in shared memory; Ud free
+    // (a) per row (one warp per row): combine U0 + a1 U1 in place, row maximum,
+    // then digits from shared memory (two passes keep the registers free)
     for (int rr = warp; rr < GM_RT; rr += GM_THREADS / 32) {
-      int64_t R = r0 + rr;
+      float2* row0 = raw0 + rr * K16;
       float mx = 0.0f;
-      if (R < n) {
-        for (int k = lane; k < K; k += 32) {
-          int kk = k / p, l = k - kk * p;
-          mx = fmaxf(mx, fabsf(a.U[kk][R * p + l].x));
+      for (int k = lane; k < K16; k += 32) {
+        float2 x = row0[k];
+        if (two) {
+          x = df_add(x, df_mul(a.a1, raw1[rr * K16 + k]));
+          row0[k] = x;
         }
+        mx = fmaxf(mx, fabsf(x.x));
       }
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) Er[rr] = exponent_above(mx);
-    }
-    __syncthreads();
-    // (b) digits of the row tile: one thread per (row, pair of columns)
-    for (int e = tid; e < GM_RT * (K16 / 2); e += GM_THREADS) {
-      int rr = e / (K16 / 2);
-      int k = 2 * (e - rr * (K16 / 2));
-      int64_t R = r0 + rr;
-      float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
-      if (R < n) {
-        if (k < K) {
-          int kk = k / p, l = k - kk * p;
-          x0 = a.U[kk][R * p + l];
-        }
-        if (k + 1 < K) {
-          int kk = (k + 1) / p, l = (k + 1) - kk * p;
-          x1 = a.U[kk][R * p + l];
-        }
-      }
-      int E = Er[rr];
-      float d0[ND], d1[ND];
-      digits7(x0.x, x0.y, E, d0);
-      digits7(x1.x, x1.y, E, d1);
+      const int E = exponent_above(mx);
+      if (lane == 0) Er[rr] = E;
+      __syncwarp();
+      for (int cp = lane; 2 * cp < K16; cp += 32) {
+        const float4 xx = *reinterpret_cast<const float4*>(row0 + 2 * cp);
+        float d0[ND], d1[ND];
+        digits7(xx.x, xx.y, E, d0);
+        digits7(xx.z, xx.w, E, d1);
 #pragma unroll
-      for (int i = 0; i < ND; ++i)
-        *reinterpret_cast<uint32_t*>(Ud + ((size_t)i * GM_RT + rr) * uds + k) = pack_bf16x2(d0[i], d1[i]);
+        for (int i = 0; i < ND; ++i)
+          *reinterpret_cast<uint32_t*>(Ud + ((size_t)i * GM_RT + rr) * uds + 2 * cp) =
+              pack_bf16x2(d0[i], d1[i]);
+      }
     }
-    __syncthreads();
+    __syncthreads();  // digits ready, raw buffers free: prefetch the next tile
+    if (tile + gridDim.x < ntiles) gm_stage(a, n, p, K16, (tile + gridDim.x) * GM_RT, raw0, raw1);
     // (c) tensor-core products, exact per digit-pair group
     float acc[ND][2][4];
 #pragma unroll
@@ -305,6 +325,7 @@ oz_gemm_kernel(int64_t n, int p, int p16, int nk, int K16, OzGemmArgs a) {
       }
     }
   }
+  cp_async_wait_all();
   if (a.dot_part) {
     __shared__ float2 red[2][GM_THREADS / 32];
     for (int o = 16; o > 0; o >>= 1) {
@@ -336,13 +357,32 @@ oz_gemm_kernel(int64_t n, int p, int p16, int nk, int K16, OzGemmArgs a) {
 // GR_KC = 64 processed by the blocks of blockIdx.x in turn. 16 warps, each a
 // 16 x 16 output tile (2 n-tiles); per chunk the column exponents are taken
 // over the chunk's rows, so each chunk's digit products are exact, and the
-// chunk results are accumulated in df64 registers.
+// chunk results are accumulated in df64 registers. The next chunk's raw rows
+// are fetched with cp.async while the current chunk is on the tensor cores.
 // ---------------------------------------------------------------------------
 constexpr int GR_KC = 64;
 constexpr int GR_THREADS = 512;
 constexpr int GR_STRIDE = 64 + 8;
 
-size_t oz_gram_smem() { return (size_t)2 * ND * GR_KC * GR_STRIDE * 2 + 4 * 64 * sizeof(int); }
+size_t oz_gram_smem() {
+  return (size_t)2 * ND * GR_KC * GR_STRIDE * 2 + (size_t)2 * GR_KC * 64 * sizeof(float2) +
+         (4 * 128 + 4 * 64) * sizeof(int) + 64;
+}
+
+__device__ __forceinline__ void gr_stage(int64_t n, int p, int q, const float2* U, const float2* V,
+                                         int i0, int j0, int64_t r0, float2* rawU, float2* rawV) {
+  for (int e = threadIdx.x; e < 2 * GR_KC * 64; e += GR_THREADS) {
+    const bool isv = e >= GR_KC * 64;
+    const int e2 = isv ? e - GR_KC * 64 : e;
+    const int r = e2 >> 6, c = e2 & 63;
+    const int64_t R = r0 + r;
+    const int ld = isv ? q : p, c0 = isv ? j0 : i0;
+    const bool ok = R < n && c0 + c < ld;
+    const float2* src = isv ? V : U;
+    cp_async8((isv ? rawV : rawU) + e2, src + (ok ? R * ld + c0 + c : 0), ok);
+  }
+  cp_async_commit();
+}
 
 __global__ void __launch_bounds__(GR_THREADS)
 oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
@@ -350,12 +390,12 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
   extern __shared__ __align__(16) unsigned char smem[];
   __nv_bfloat16* Ud = reinterpret_cast<__nv_bfloat16*>(smem);
   __nv_bfloat16* Vd = Ud + (size_t)ND * GR_KC * GR_STRIDE;
-  int* mxu = reinterpret_cast<int*>(Vd + (size_t)ND * GR_KC * GR_STRIDE);
-  int* mxv = mxu + 64;
-  int* Eu = mxv + 64;
+  float2* rawU = reinterpret_cast<float2*>(Vd + (size_t)ND * GR_KC * GR_STRIDE);
+  float2* rawV = rawU + GR_KC * 64;
+  int* cmx = reinterpret_cast<int*>(rawV + GR_KC * 64);  // [4][128] partial column maxima
+  int* Eu = cmx + 4 * 128;
   int* Ev = Eu + 64;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // output block
   int bi, bj;
   {
     int b = blockIdx.y;
@@ -380,47 +420,48 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
 #pragma unroll
     for (int e = 0; e < 4; ++e) res[t][e] = make_float2(0.f, 0.f);
   const int64_t nchunks = (n + GR_KC - 1) / GR_KC;
+  if ((int64_t)blockIdx.x < nchunks)
+    gr_stage(n, p, q, U, V, i0, j0, (int64_t)blockIdx.x * GR_KC, rawU, rawV);
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int64_t r0 = ch * GR_KC;
+    cp_async_wait_all();
     __syncthreads();
-    if (tid < 128) mxu[tid] = 0;  // mxu and mxv are adjacent
-    __syncthreads();
-    // (a) column maxima of |hi| over the chunk
-    for (int e = tid; e < GR_KC * 64; e += GR_THREADS) {
-      int r = e >> 6, c = e & 63;
-      int64_t R = r0 + r;
-      if (R < n) {
-        if (i0 + c < p) atomicMax(&mxu[c], __float_as_int(fabsf(U[R * p + i0 + c].x)));
-        if (j0 + c < q) atomicMax(&mxv[c], __float_as_int(fabsf(V[R * q + j0 + c].x)));
-      }
+    // (a) column maxima of |hi|: thread -> (column c of [U V], group of 16 rows)
+    {
+      const int c = tid & 127, g = tid >> 7;
+      const float2* src = c < 64 ? rawU : rawV;
+      const int cc = c & 63;
+      float mx = 0.f;
+#pragma unroll 4
+      for (int r = g * 16; r < g * 16 + 16; ++r) mx = fmaxf(mx, fabsf(src[r * 64 + cc].x));
+      cmx[g * 128 + c] = __float_as_int(mx);
     }
     __syncthreads();
-    if (tid < 64) Eu[tid] = exponent_above(__int_as_float(mxu[tid]));
-    else if (tid < 128) Ev[tid - 64] = exponent_above(__int_as_float(mxv[tid - 64]));
+    if (tid < 128) {
+      float mx = fmaxf(fmaxf(__int_as_float(cmx[tid]), __int_as_float(cmx[128 + tid])),
+                       fmaxf(__int_as_float(cmx[256 + tid]), __int_as_float(cmx[384 + tid])));
+      if (tid < 64) Eu[tid] = exponent_above(mx);
+      else Ev[tid - 64] = exponent_above(mx);
+    }
     __syncthreads();
     // (b) digits: one thread per (row, pair of columns), U then V
     for (int e = tid; e < 2 * GR_KC * 32; e += GR_THREADS) {
       const bool isv = e >= GR_KC * 32;
-      int e2 = isv ? e - GR_KC * 32 : e;
-      int r = e2 >> 5, c = 2 * (e2 & 31);
-      int64_t R = r0 + r;
-      const float2* src = isv ? V : U;
-      const int ld = isv ? q : p, c0 = isv ? j0 : i0;
-      float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
-      if (R < n) {
-        if (c0 + c < ld) x0 = src[R * ld + c0 + c];
-        if (c0 + c + 1 < ld) x1 = src[R * ld + c0 + c + 1];
-      }
+      const int e2 = isv ? e - GR_KC * 32 : e;
+      const int r = e2 >> 5, c = 2 * (e2 & 31);
+      const float2* src = isv ? rawV : rawU;
+      const float4 xx = *reinterpret_cast<const float4*>(src + r * 64 + c);
       const int* Ex = isv ? Ev : Eu;
       float d0[ND], d1[ND];
-      digits7(x0.x, x0.y, Ex[c], d0);
-      digits7(x1.x, x1.y, Ex[c + 1], d1);
+      digits7(xx.x, xx.y, Ex[c], d0);
+      digits7(xx.z, xx.w, Ex[c + 1], d1);
       __nv_bfloat16* dst = isv ? Vd : Ud;
 #pragma unroll
       for (int i = 0; i < ND; ++i)
         *reinterpret_cast<uint32_t*>(dst + ((size_t)i * GR_KC + r) * GR_STRIDE + c) = pack_bf16x2(d0[i], d1[i]);
     }
-    __syncthreads();
+    __syncthreads();  // digits ready, raw buffers free: prefetch the next chunk
+    if (ch + gridDim.x < nchunks)
+      gr_stage(n, p, q, U, V, i0, j0, (ch + gridDim.x) * GR_KC, rawU, rawV);
     if (active) {
       float acc[ND][2][4];
 #pragma unroll
@@ -466,6 +507,7 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
         }
     }
   }
+  cp_async_wait_all();
   if (active) {
     float2* out = part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * 64 * 64;
 #pragma unroll
@@ -517,17 +559,19 @@ __global__ void oz_gram_reduce_kernel(int p, int q, int nsplit, int nblk, int sy
 int pad16(int x) { return (x + 15) / 16 * 16; }
 
 size_t oz_rhs_bytes(int p, int nk) {
-  return (size_t)ND * pad16(p) * pad16(nk * p) * sizeof(__nv_bfloat16) + pad16(p) * sizeof(int) + 256;
+  (void)nk;
+  return (size_t)ND * pad16(p) * pad16(p) * sizeof(__nv_bfloat16) + pad16(p) * sizeof(int) + 256;
 }
 
 gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const double* const M[2],
                    const double s[2], int ne, const float2* const E[2], const float2 ce[2],
                    float2* out, float2* dot_part, const float2* dot_with, bool dot_self,
                    void* rhs_ws, cudaStream_t st, int* nparts) {
-  if (nk < 1 || nk > 2 || ne < 0 || ne > 2 || nk * p > 256) return GSI_ERR_ARG;
-  if (nk == 2 && pad16(2 * p) > 128) {
-    // shared memory holds K <= 128: OUT = U_0 M_0 + E terms, then OUT += U_1 M_1
-    if (pad16(p) > 64 && (U[0] == out || U[1] == out)) return GSI_ERR_ARG;
+  if (nk < 1 || nk > 2 || ne < 0 || ne > 2 || p < 1 || p > 128) return GSI_ERR_ARG;
+  bool fuse = nk == 2 && M[1] == M[0] && s[0] != 0.0;
+  if (fuse && oz_gemm_smem(pad16(p), std::min(64, pad16(p)), 2) > 227 * 1024) fuse = false;
+  if (nk == 2 && !fuse) {
+    // OUT = s0 U0 M0 + E terms, then OUT += s1 U1 M1
     const float2* U0[2] = {U[0], U[0]};
     const double* M0[2] = {M[0], M[0]};
     double s0[2] = {s[0], 0.0};
@@ -541,16 +585,21 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
     return oz_gemm(n, p, 1, U1, M1, s1, 1, E1, c1, out, dot_part, dot_with, dot_self, rhs_ws, st,
                    nparts);
   }
-  const int p16 = pad16(p), K16 = pad16(nk * p);
+  const int p16 = pad16(p), K16 = p16;
+  const int ncs = (p16 + 63) / 64;
+  if (ncs > 1)
+    for (int k = 0; k < nk; ++k)
+      if (U[k] == out) return GSI_ERR_ARG;  // column slices would race on in-place rows
   __nv_bfloat16* Md = reinterpret_cast<__nv_bfloat16*>(rhs_ws);
   int* F = reinterpret_cast<int*>(reinterpret_cast<char*>(rhs_ws) +
                                   (size_t)ND * p16 * K16 * sizeof(__nv_bfloat16));
-  oz_prep_rhs_kernel<<<p16, 128, 0, st>>>(p, p16, nk, K16, M[0], nk > 1 ? M[1] : M[0], s[0],
-                                          nk > 1 ? s[1] : 0.0, Md, F);
+  oz_prep_rhs_kernel<<<p16, 128, 0, st>>>(p, p16, 1, K16, M[0], M[0], s[0], 0.0, Md, F);
   GSI_LAUNCH_CHECK();
   OzGemmArgs a{};
   a.U[0] = U[0];
-  a.U[1] = nk > 1 ? U[1] : U[0];
+  a.U[1] = fuse ? U[1] : U[0];
+  a.fuse_u1 = fuse ? 1 : 0;
+  a.a1 = fuse ? df_from_double(s[1] / s[0]) : make_float2(0.f, 0.f);
   a.ne = ne;
   for (int m = 0; m < ne; ++m) {
     a.E[m] = E[m];
@@ -562,20 +611,18 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   a.dot_part = dot_part;
   a.dot_with = dot_with;
   a.dot_self = dot_self ? 1 : 0;
-  const int ncs = (p16 + 63) / 64;
   const int NCmax = std::min(64, p16);
-  size_t smem = oz_gemm_smem(K16, NCmax);
-  if (ncs > 1)
-    for (int k = 0; k < nk; ++k)
-      if (U[k] == out) return GSI_ERR_ARG;  // column slices would race on in-place rows
+  size_t smem = oz_gemm_smem(K16, NCmax, fuse ? 2 : 1);
   GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
   int64_t ntiles = (n + GM_RT - 1) / GM_RT;
-  int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  int per_sm = 1;
+  GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oz_gemm_kernel, GM_THREADS, smem));
+  per_sm = std::max(per_sm, 1);
   int gx = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * per_sm / ncs);
   gx = std::max(gx, 1);
   if (nparts) *nparts = gx * ncs;
-  oz_gemm_kernel<<<dim3(gx, ncs), GM_THREADS, smem, st>>>(n, p, p16, nk, K16, a);
+  oz_gemm_kernel<<<dim3(gx, ncs), GM_THREADS, smem, st>>>(n, p, p16, K16, a);
   GSI_LAUNCH_CHECK();
   return GSI_OK;
 }

@@ -8,7 +8,9 @@
 namespace gsi {
 
 struct OzGemmArgs {
-  const float2* U[2];        // n x p df64 blocks (left operands, concatenated along K)
+  const float2* U[2];        // n x p df64 blocks; the left operand is U0 (+ a1 U1 if fuse_u1)
+  int fuse_u1;
+  float2 a1;
   int ne;                    // elementwise terms (0..2)
   const float2* E[2];        // n x p df64 blocks
   float2 ce[2];              // df64 scalars of the elementwise terms
@@ -23,6 +25,8 @@ struct OzGemmArgs {
 int pad16(int x);
 size_t oz_rhs_bytes(int p, int nk);
 // OUT = sum_{k<nk} U_k (s_k M_k) + sum_{e<ne} ce_e E_e; M_k float64 p x p (device).
+// With nk = 2 and M_1 == M_0 the left operand U_0 + (s_1/s_0) U_1 is formed in
+// df64 on the fly (one product of contraction length p).
 // rhs_ws: oz_rhs_bytes(p, nk) bytes of device scratch for the right operand's digits.
 // dot_part (optional): 2 * (*nparts) df64 partial sums.
 gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const double* const M[2],

@@ -127,3 +127,22 @@ def test_oz_gram(G, n, p, q, sym):
     assert np.all(np.abs(got - ref) <= 2.0 ** -44 * chunk_bound + 2.0 ** -46 * absprod)
     if sym:
         assert np.array_equal(got, got.T)
+
+
+@pytest.mark.parametrize("n,p", [(5000, 64), (3001, 17), (4000, 128)])
+def test_oz_gemm_fused_left_sum(G, n, p):
+    """Same right operand for both terms: (U0 + a U1) M is formed with the sum
+    taken in df64 before the split (the retraction X <- (X + tD) M)."""
+    torch, gsi = G
+    rng = np.random.default_rng(p)
+    U0 = _exact(gsi, rng.standard_normal((n, p)))
+    U1 = _exact(gsi, rng.standard_normal((n, p)) * 1e-3)
+    M = rng.standard_normal((p, p))
+    t = 0.37
+    Md = torch.from_numpy(M).cuda()
+    out = torch.zeros((n, p, 2), dtype=torch.float32, device="cuda")
+    gsi.oz_gemm(_df_dev(torch, gsi, U0), Md, out, s0=1.0, U1=_df_dev(torch, gsi, U1), M1=Md, s1=t)
+    ref = (U0 + t * U1) @ M
+    got = gsi.from_df(out.cpu().numpy())
+    bound = (np.abs(U0) + t * np.abs(U1)).max(1, keepdims=True) * np.abs(M).max(0, keepdims=True) * p * 2.0 ** -44
+    assert np.all(np.abs(got - ref) <= bound)
