@@ -264,6 +264,24 @@ gsi_status gsi_oz_gemm(int64_t n, int32_t p, int32_t nk, const float* U0, const 
 gsi_status gsi_oz_gram(int64_t n, int32_t p, int32_t q, const float* U, const float* V,
                        int32_t sym, double* G, void* stream);
 
+/* Allocation-free variant of gsi_oz_gram (no counterpart in the paper).
+ * For callers that may not allocate device memory when they call in: code
+ * recorded into a CUDA graph whose memory pool the caller does not own,
+ * real-time or embedded hosts that forbid allocation after start-up, and
+ * threads without access to the process's allocator. Arguments and result
+ * are those of gsi_oz_gram. The per-block partial sums use one static device
+ * array of 8 MiB, which every GPU that loads this library keeps until the
+ * process exits; calls whose partials would exceed it (more than 256 SMs)
+ * return GSI_ERR_ARG with a message in gsi_last_error(). The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. Every
+ * call shares the array and overwrites it (it is cleared on each call), so
+ * calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads -- race; serialise them. No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, const float* V,
+                               int32_t sym, double* G, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
