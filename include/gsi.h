@@ -45,7 +45,9 @@ typedef enum {
 } gsi_status;
 
 typedef enum { GSI_CSR = 0, GSI_SELL = 1 } gsi_format;
-typedef enum { GSI_SD = 0, GSI_CG = 1 } gsi_method;
+/* GSI_CHEB: the Chebyshev-filtered subspace iteration the paper compares
+ * against (Alg. 1 with the filter of Eq. (optimal_poly)). */
+typedef enum { GSI_SD = 0, GSI_CG = 1, GSI_CHEB = 2 } gsi_method;
 /* Arithmetic of the n x p block work. GSI_PREC_DF64: blocks stored as
  * float32 pairs (48-bit significand), products on the BF16 tensor cores with
  * error-free digit splitting (float64-class results); GSI_PREC_F64: native
@@ -80,6 +82,12 @@ typedef struct {
   int32_t recompute_every; /* explicit Y = AX every k iterations; 0 = only when the step is tiny */
   int32_t explicit_ax;     /* 1: explicit AX every iteration ("RCG(+)", Sec. 6.4) */
   int32_t precision;       /* gsi_precision, default GSI_PREC_DF64 */
+  /* GSI_CHEB only: filter degree d, the unwanted interval [cheb_lo, cheb_hi]
+   * (lambda_n and lambda_{p+1}: c = (lo+hi)/2, h = (hi-lo)/2) and the scaling
+   * point cheb_scale (an estimate of lambda_1); one iteration = Rayleigh-Ritz,
+   * residual test, d filter matvecs and an orthonormalisation. */
+  int32_t cheb_degree;
+  double cheb_lo, cheb_hi, cheb_scale;
 } gsi_opts;
 
 typedef struct {

@@ -355,6 +355,23 @@ __global__ void pp_axpby_kernel(int p, double a, const double* X, double b, cons
   out[e] = a * X[e] + (Y ? b * Y[e] : 0.0);
 }
 
+__global__ void combine3_kernel(int64_t count, double a, const double* W, double b, const double* Z,
+                                double e, const double* Zp, double* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double v = a * W[i] + b * Z[i];
+  if (Zp) v += e * Zp[i];
+  out[i] = v;
+}
+
+gsi_status combine3(int64_t count, double a, const double* W, double b, const double* Z, double e,
+                    const double* Zp, double* out, cudaStream_t st) {
+  if (count <= 0) return GSI_OK;
+  combine3_kernel<<<ceil_div(count, 256), 256, 0, st>>>(count, a, W, b, Z, e, Zp, out);
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
 gsi_status pp_gemm(int p, double alpha, const double* A, const double* B, double beta,
                    const double* E, double* out, cudaStream_t st) {
   pp_gemm_kernel<<<ceil_div(p * p, 64), 64, 0, st>>>(p, alpha, A, B, beta, E, out);

@@ -28,6 +28,9 @@ gsi_status dots(int64_t n, int p, int ndots, const double* A0, const double* B0,
                 const double* A1, const double* B1, const double* Rnorm, double* out,
                 double* scratch, cudaStream_t st);
 
+// out = a W + b Z + e Zp elementwise (Zp may be null)
+gsi_status combine3(int64_t count, double a, const double* W, double b, const double* Z, double e,
+                    const double* Zp, double* out, cudaStream_t st);
 // p x p float64 products over many blocks: out = alpha A B + beta E; out = a X + b Y
 gsi_status pp_gemm(int p, double alpha, const double* A, const double* B, double beta,
                    const double* E, double* out, cudaStream_t st);

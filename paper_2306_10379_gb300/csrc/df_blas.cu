@@ -223,6 +223,25 @@ gsi_status df_axpby(int64_t count, float2 a, const float2* x, float2 b, float2* 
   return GSI_OK;
 }
 
+// out = a W + b Z + e Zp (df64 scalars; Zp may be null) -- one step of the
+// Chebyshev three-term recurrence after the matvec W = A Z
+__global__ void df_combine3_kernel(int64_t count, float2 a, const float2* W, float2 b,
+                                   const float2* Z, float2 e, const float2* Zp, float2* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float2 v = df_add(df_mul(a, W[i]), df_mul(b, Z[i]));
+  if (Zp) v = df_add(v, df_mul(e, Zp[i]));
+  out[i] = v;
+}
+
+gsi_status df_combine3(int64_t count, float2 a, const float2* W, float2 b, const float2* Z, float2 e,
+                       const float2* Zp, float2* out, cudaStream_t st) {
+  if (count <= 0) return GSI_OK;
+  df_combine3_kernel<<<ceil_div(count, 256), 256, 0, st>>>(count, a, W, b, Z, e, Zp, out);
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
 __global__ void df_sum_parts_kernel(int nparts, const float2* parts, double* out) {
   if (threadIdx.x != 0) return;
   float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);

@@ -54,6 +54,9 @@ gsi_status df_dots(int64_t n, int p, const float2* A0, const float2* B0, const f
                    cudaStream_t st);
 // y = a*x + b*y elementwise (df64 scalars)
 gsi_status df_axpby(int64_t count, float2 a, const float2* x, float2 b, float2* y, cudaStream_t st);
+// out = a W + b Z + e Zp elementwise (df64 scalars; Zp may be null)
+gsi_status df_combine3(int64_t count, float2 a, const float2* W, float2 b, const float2* Z, float2 e,
+                       const float2* Zp, float2* out, cudaStream_t st);
 // sum of df64 partial pairs into out[0..1] (float64)
 gsi_status df_sum_parts(int nparts, const float2* parts, double* out, cudaStream_t st);
 

@@ -426,6 +426,15 @@ small_df_kernel(int mode, int p, const double* C, const double* B, const double*
   long long t0 = clock64();
   eig_refined(p, B, w, red, out + 8);
   long long t1 = clock64();
+  if (mode == 2) {
+    // Rayleigh-Ritz: eigenvectors of C (here passed as B) into M (float64),
+    // eigenvalues into XD[0..p) (unsorted; column i of M belongs to XD[i])
+    for (int e = threadIdx.x; e < q; e += blockDim.x) M[e] = df_to_double(w.Vd[e]);
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+      const_cast<double*>(XD)[i] = df_to_double(w.Bd[i * p + i]);
+    if (threadIdx.x == 0) out[3] = 0.0;
+    return;
+  }
   if (mode == 1) {
     int st = inv_sqrt_in_basis(p, w, M, &flag);
     if (threadIdx.x == 0) {

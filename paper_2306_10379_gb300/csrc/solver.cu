@@ -435,6 +435,106 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
   return GSI_OK;
 }
 
+__global__ void diag_kernel(int p, const double* d, double* D) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p * p) return;
+  int i = e / p, j = e - i * p;
+  D[e] = (i == j) ? d[i] : 0.0;
+}
+
+// out = a W + b Z + e Zp in the context's block type
+gsi_status op_combine3(gsi_ctx* c, double a, const void* W, double b, const void* Z, double e,
+                       const void* Zp, void* outp) {
+  prof_begin(c);
+  gsi_status s;
+  const int64_t cnt = c->n * c->p;
+  if (c->emu)
+    s = df_combine3(cnt, df_from_double(a), (const float2*)W, df_from_double(b), (const float2*)Z,
+                    df_from_double(e), (const float2*)Zp, (float2*)outp, c->st);
+  else
+    s = combine3(cnt, a, (const double*)W, b, (const double*)Z, e, (const double*)Zp, (double*)outp,
+                 c->st);
+  prof_end(c, GSI_K_REDUCE, (Zp ? 4 : 3) * blk_bytes(c), 0.0);
+  return s;
+}
+
+// One iteration of Chebyshev-filtered subspace iteration (Alg. 1 with the
+// filter C_d((t - c)/h) / C_d((lambda_1 - c)/h) of Eq. (optimal_poly)):
+// Rayleigh-Ritz on span(X), residual test, Z = p_d(A) X by the three-term
+// recurrence (sigma_{k+1} = 1/(2e - sigma_k), e = (lambda_1 - c)/h), then an
+// orthonormal basis of span(Z).
+gsi_status iterate_cheb(gsi_ctx* c, bool* stop) {
+  const int p = c->p;
+  *stop = false;
+  // Rayleigh-Ritz with the fresh Y = A X
+  GSI_TRY(op_gram(c, c->X, c->Y, true, c->Cm));
+  prof_begin(c);
+  if (c->emu) {
+    GSI_TRY(small_step_df(2, p, nullptr, c->Cm, nullptr, nullptr, nullptr, c->XDm, c->Bm, c->out,
+                          c->small_ws, c->st));
+  } else {
+    GSI_TRY(small_eig(p, c->Cm, c->XDm, c->Bm, c->small_ws, c->st));
+  }
+  diag_kernel<<<ceil_div(p * p, 256), 256, 0, c->st>>>(p, c->XDm, c->Gm);
+  note_launch();
+  prof_end(c, GSI_K_SMALL, 0.0, 0.0);
+  GSI_TRY(op_blockmul(c, 1, c->X, c->Bm, 1.0, nullptr, nullptr, 0.0, 0, nullptr, 0.0, nullptr, 0.0,
+                      c->Xn, false, nullptr));
+  std::swap(c->X, c->Xn);
+  GSI_TRY(op_blockmul(c, 1, c->Y, c->Bm, 1.0, nullptr, nullptr, 0.0, 0, nullptr, 0.0, nullptr, 0.0,
+                      c->Yn, false, nullptr));
+  std::swap(c->Y, c->Yn);
+  // R = Y - X diag(theta), ||R||_F
+  GSI_TRY(op_blockmul(c, 1, c->X, c->Gm, -1.0, nullptr, nullptr, 0.0, 1, c->Y, 1.0, nullptr, 0.0,
+                      c->R, true, nullptr));
+  GSI_TRY(readback(c, c->dout, 1));
+  const double rr = c->host[0];
+  GSI_TRY(op_rowinf(c, c->R));
+  GSI_TRY(readback(c, c->dout + 2, 1));
+  const double rinf = c->host[0];
+  if (!isfinite(rr)) return GSI_ERR_NONFINITE;
+  if (c->res0_inf < 0.0) c->res0_inf = rinf;
+  c->rel = sqrt(rr) / c->anorm;
+  c->rel_inf = c->res0_inf > 0.0 ? rinf / c->res0_inf : 0.0;
+  // the Ritz basis is kept in C for fill_info: C <- diag(theta)
+  GSI_CUDA_TRY(cudaMemcpyAsync(c->Cm, c->Gm, (size_t)p * p * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->st));
+  if (c->rel <= c->o.tol || c->iters >= c->o.max_iters) {
+    c->converged = c->rel <= c->o.tol;
+    *stop = true;
+    return GSI_OK;
+  }
+  // filter: Z_1 = (sigma_1 / h)(A - cI) X, Z_{k+1} = (2 sigma_{k+1} / h)(A - cI) Z_k - sigma_k sigma_{k+1} Z_{k-1}
+  const double cc = 0.5 * (c->o.cheb_hi + c->o.cheb_lo), hh = 0.5 * (c->o.cheb_hi - c->o.cheb_lo);
+  const double e = (c->o.cheb_scale - cc) / hh;
+  double sigma = 1.0 / e;
+  void* bufs[4] = {c->X, c->D, c->P, c->R};
+  int ip = 0, ic = 1;
+  GSI_TRY(op_matvec(c, bufs[ip], c->W));
+  GSI_TRY(op_combine3(c, sigma / hh, c->W, -cc * sigma / hh, bufs[ip], 0.0, nullptr, bufs[ic]));
+  for (int k = 1; k < c->o.cheb_degree; ++k) {
+    const double sn = 1.0 / (2.0 * e - sigma);
+    int nb = 0;  // a buffer holding neither Z_{k-1} nor Z_k
+    while (nb == ip || nb == ic) ++nb;
+    GSI_TRY(op_matvec(c, bufs[ic], c->W));
+    GSI_TRY(op_combine3(c, 2.0 * sn / hh, c->W, -2.0 * sn * cc / hh, bufs[ic], -sigma * sn, bufs[ip],
+                        bufs[nb]));
+    ip = ic;
+    ic = nb;
+    sigma = sn;
+  }
+  // the filtered block becomes X (buffers are only re-labelled)
+  c->X = bufs[ic];
+  c->D = bufs[(ic + 1) % 4];
+  c->P = bufs[(ic + 2) % 4];
+  c->R = bufs[(ic + 3) % 4];
+  GSI_TRY(orthonormalize(c));
+  GSI_TRY(op_matvec(c, c->X, c->Y));
+  c->y_fresh = true;
+  c->iters++;
+  return GSI_OK;
+}
+
 void fill_info(gsi_ctx* c, gsi_info* info) {
   if (!info) return;
   info->iters = c->iters;
@@ -493,6 +593,10 @@ gsi_status gsi_default_opts(gsi_opts* o) {
   o->recompute_every = 50;
   o->explicit_ax = 0;
   o->precision = GSI_PREC_DF64;
+  o->cheb_degree = 8;
+  o->cheb_lo = 0.0;
+  o->cheb_hi = 0.0;
+  o->cheb_scale = 0.0;
   return GSI_OK;
 }
 
@@ -531,7 +635,11 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
   gsi_opts opts;
   gsi_default_opts(&opts);
   if (o) opts = *o;
-  if ((opts.method != GSI_SD && opts.method != GSI_CG) || (opts.which != 1 && opts.which != -1) ||
+  if (opts.method == GSI_CHEB &&
+      (opts.cheb_degree < 1 || !(opts.cheb_hi > opts.cheb_lo) || !(opts.cheb_scale > opts.cheb_hi)))
+    return GSI_ERR_ARG;
+  if ((opts.method != GSI_SD && opts.method != GSI_CG && opts.method != GSI_CHEB) ||
+      (opts.which != 1 && opts.which != -1) ||
       opts.max_iters < 0 || !(opts.tol >= 0.0) ||
       (opts.precision != GSI_PREC_DF64 && opts.precision != GSI_PREC_F64))
     return GSI_ERR_ARG;
@@ -661,7 +769,7 @@ gsi_status gsi_step(gsi_ctx* c, int32_t nsteps, gsi_info* info) {
   if (!c || nsteps < 0) return GSI_ERR_ARG;
   for (int i = 0; i < nsteps; ++i) {
     bool stop = false;
-    GSI_TRY(iterate(c, &stop));
+    GSI_TRY(c->o.method == GSI_CHEB ? iterate_cheb(c, &stop) : iterate(c, &stop));
     if (stop) break;
   }
   fill_info(c, info);
@@ -672,7 +780,7 @@ gsi_status gsi_solve(gsi_ctx* c, gsi_info* info) {
   if (!c) return GSI_ERR_ARG;
   for (;;) {
     bool stop = false;
-    GSI_TRY(iterate(c, &stop));
+    GSI_TRY(c->o.method == GSI_CHEB ? iterate_cheb(c, &stop) : iterate(c, &stop));
     if (stop) break;
   }
   fill_info(c, info);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libgsi.so")
 GSI_OK, GSI_ERR_ARG, GSI_ERR_CUDA, GSI_ERR_OOM, GSI_ERR_NOCONV, GSI_ERR_BREAKDOWN, \
     GSI_ERR_NONFINITE, GSI_ERR_TIMEOUT = range(8)
 GSI_CSR, GSI_SELL = 0, 1
-GSI_SD, GSI_CG = 0, 1
+GSI_SD, GSI_CG, GSI_CHEB = 0, 1, 2
 GSI_PREC_DF64, GSI_PREC_F64 = 0, 1
 KERNEL_CLASSES = ["spmm", "gram", "blockmul", "small", "reduce"]
 
@@ -50,7 +50,9 @@ class Opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("which", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("anorm", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("k_restart", ctypes.c_int32), ("recompute_every", ctypes.c_int32),
-                ("explicit_ax", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("explicit_ax", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("cheb_degree", ctypes.c_int32), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double), ("cheb_scale", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -296,7 +298,7 @@ class Solver:
 
     def __init__(self, A, p, X0, method="sd", which=1, tol=1e-8, anorm=0.0, max_iters=10000,
                  k_restart=0, recompute_every=50, explicit_ax=False, fmt="csr", precision="df64",
-                 stream=None):
+                 cheb_degree=8, cheb_interval=(0.0, 0.0), cheb_scale=0.0, stream=None):
         import torch
         L = lib()
         self._keep = []
@@ -313,7 +315,10 @@ class Solver:
         m = Matrix(GSI_SELL if fmt == "sell" else GSI_CSR, int(A.n), nnz, rp, ci, va, 32, 32, 1 if on_dev else 0)
         o = Opts()
         L.gsi_default_opts(ctypes.byref(o))
-        o.method = GSI_CG if method == "cg" else GSI_SD
+        o.method = {"sd": GSI_SD, "cg": GSI_CG, "cheb": GSI_CHEB}[method]
+        o.cheb_degree = int(cheb_degree)
+        o.cheb_lo, o.cheb_hi = float(cheb_interval[0]), float(cheb_interval[1])
+        o.cheb_scale = float(cheb_scale)
         o.which = int(which)
         o.tol = float(tol)
         o.anorm = float(anorm)
