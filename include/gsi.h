@@ -44,18 +44,28 @@ typedef enum {
   GSI_ERR_TIMEOUT = 7     /* a bounded device-side wait expired */
 } gsi_status;
 
-typedef enum { GSI_CSR = 0, GSI_SELL = 1 } gsi_format;
+typedef enum { GSI_CSR = 0, GSI_SELL = 1, GSI_DENSE = 2 } gsi_format;
 /* GSI_CHEB: the Chebyshev-filtered subspace iteration the paper compares
  * against (Alg. 1 with the filter of Eq. (optimal_poly)). */
 typedef enum { GSI_SD = 0, GSI_CG = 1, GSI_CHEB = 2 } gsi_method;
 /* Arithmetic of the n x p block work. GSI_PREC_DF64: blocks stored as
  * float32 pairs (48-bit significand), products on the BF16 tensor cores with
- * error-free digit splitting (float64-class results); GSI_PREC_F64: native
- * float64 on the float64 pipe. The p x p step is float64 in both. */
-typedef enum { GSI_PREC_DF64 = 0, GSI_PREC_F64 = 1 } gsi_precision;
+ * error-free digit splitting into 7 digits (float64-class results);
+ * GSI_PREC_F64: native float64 on the float64 pipe. GSI_PREC_MIXED: as
+ * GSI_PREC_DF64, but the operator apply A X of a dense A uses 3 digits per
+ * operand (bf16-level products summed exactly in fp32, ~2^-21 relative) until
+ * ||R||_F/anorm <= mixed_switch, then a correction phase with 7-digit applies
+ * (explicit AX recomputed, CG restarted) until the tolerance; the residual,
+ * the Grams and the retraction stay float64-class throughout, so the errors
+ * of the cheap apply scale with ||D|| rather than with ||A X||. The p x p
+ * step is float64-class in all modes. */
+typedef enum { GSI_PREC_DF64 = 0, GSI_PREC_F64 = 1, GSI_PREC_MIXED = 2 } gsi_precision;
 
-/* Sparse symmetric A in full CSR storage (both triangles).
+/* Symmetric A. fmt = GSI_CSR / GSI_SELL: full CSR storage (both triangles),
  * rowptr: n+1 int64, colidx: nnz int32 (0-based), val: nnz float64.
+ * fmt = GSI_DENSE: val holds the n x n matrix row-major (float64), rowptr,
+ * colidx and nnz are ignored; the block matvec is then the dense product
+ * A X (computed as A^T X, the contraction over n).
  * on_device = 0: the three arrays are host memory; 1: device memory.
  * fmt = GSI_SELL asks the context to convert A to SELL-C-sigma
  * (chunk height sell_C = 32, sorting window sell_sigma) for its SpMM.
@@ -88,6 +98,7 @@ typedef struct {
    * residual test, d filter matvecs and an orthonormalisation. */
   int32_t cheb_degree;
   double cheb_lo, cheb_hi, cheb_scale;
+  double mixed_switch;     /* GSI_PREC_MIXED: residual at which the 7-digit phase starts (1e-5) */
 } gsi_opts;
 
 typedef struct {
@@ -271,6 +282,14 @@ gsi_status gsi_oz_gemm(int64_t n, int32_t p, int32_t nk, const float* U0, const 
  * device memory (stream-ordered allocation). */
 gsi_status gsi_oz_gram(int64_t n, int32_t p, int32_t q, const float* U, const float* V,
                        int32_t sym, double* G, void* stream);
+
+/* Dense block matvec W = A X for a symmetric n x n A (df64, row-major),
+ * computed as A^T X with the contraction over n cut into 64-row chunks, each
+ * chunk's digit products exact on the tensor cores. nd = 7: float64-class;
+ * nd = 3: bf16-level products (the mixed-precision iterations). X and W are
+ * n x p df64 (p <= 128). Uses temporary device memory (stream-ordered). */
+gsi_status gsi_oz_dense_apply(int64_t n, int32_t p, const float* A, const float* X, float* W,
+                              int32_t nd, void* stream);
 
 /* Allocation-free variant of gsi_oz_gram (no counterpart in the paper).
  * For callers that may not allocate device memory when they call in: code

@@ -140,4 +140,15 @@ gsi_status gsi_oz_gram(int64_t n, int32_t p, int32_t q, const float* U, const fl
                  sym != 0, G, reinterpret_cast<float2*>(g.ptr), st);
 }
 
+gsi_status gsi_oz_dense_apply(int64_t n, int32_t p, const float* A, const float* X, float* W,
+                              int32_t nd, void* stream) {
+  if (n < 1 || p < 1 || p > 128 || !A || !X || !W || (nd != 3 && nd != 7)) return GSI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ScratchGuard g(st);
+  GSI_CUDA_TRY(cudaMallocAsync(&g.ptr, std::max<size_t>(oz_gram_scratch_bytes(n, (int)n, p, false), 16), st));
+  return oz_gram(n, (int)n, p, reinterpret_cast<const float2*>(A), reinterpret_cast<const float2*>(X),
+                 false, nullptr, reinterpret_cast<float2*>(g.ptr), st, nd,
+                 reinterpret_cast<float2*>(W));
+}
+
 }  // extern "C"

@@ -355,6 +355,69 @@ __global__ void pp_axpby_kernel(int p, double a, const double* X, double b, cons
   out[e] = a * X[e] + (Y ? b * Y[e] : 0.0);
 }
 
+// Dense W = A X (A n x n row-major, X n x p): 64 x 64 output tiles, K staged
+// through shared memory 32 at a time, a 4 x 4 register tile per thread.
+__global__ void dense_gemm_kernel(int64_t n, int p, const double* __restrict__ A,
+                                  const double* __restrict__ X, double* __restrict__ W) {
+  __shared__ double As[64][33];
+  __shared__ double Xs[32][65];
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 64;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double acc[4][4] = {};
+  for (int64_t k0 = 0; k0 < n; k0 += 32) {
+    for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+      int r = e / 32, k = e % 32;
+      As[r][k] = (r0 + r < n && k0 + k < n) ? A[(r0 + r) * n + k0 + k] : 0.0;
+      int kk = e / 64, cc = e % 64;
+      Xs[kk][cc] = (k0 + kk < n && c0 + cc < p) ? X[(k0 + kk) * p + c0 + cc] : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < 32; ++k) {
+      double a[4], x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[ty * 4 + i][k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = Xs[k][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], x[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t r = r0 + ty * 4 + i;
+      int c = c0 + tx * 4 + j;
+      if (r < n && c < p) W[r * p + c] = acc[i][j];
+    }
+}
+
+gsi_status dense_gemm(int64_t n, int p, const double* A, const double* X, double* W, cudaStream_t st) {
+  if (n <= 0) return GSI_OK;
+  dim3 grid(ceil_div(n, 64), ceil_div(p, 64));
+  dense_gemm_kernel<<<grid, 256, 0, st>>>(n, p, A, X, W);
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
+__global__ void dense_absmax_kernel(int64_t n, const double* A, unsigned long long* out) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double s = 0.0;
+  for (int64_t k = 0; k < n; ++k) s += fabs(A[r * n + k]);
+  atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
+gsi_status dense_absmax(int64_t n, const double* A, unsigned long long* out, cudaStream_t st) {
+  dense_absmax_kernel<<<ceil_div(n, 128), 128, 0, st>>>(n, A, out);
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
 __global__ void combine3_kernel(int64_t count, double a, const double* W, double b, const double* Z,
                                 double e, const double* Zp, double* out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -28,6 +28,9 @@ gsi_status dots(int64_t n, int p, int ndots, const double* A0, const double* B0,
                 const double* A1, const double* B1, const double* Rnorm, double* out,
                 double* scratch, cudaStream_t st);
 
+// dense W = A X (float64), max absolute row sum of a dense A
+gsi_status dense_gemm(int64_t n, int p, const double* A, const double* X, double* W, cudaStream_t st);
+gsi_status dense_absmax(int64_t n, const double* A, unsigned long long* out, cudaStream_t st);
 // out = a W + b Z + e Zp elementwise (Zp may be null)
 gsi_status combine3(int64_t count, double a, const double* W, double b, const double* Z, double e,
                     const double* Zp, double* out, cudaStream_t st);

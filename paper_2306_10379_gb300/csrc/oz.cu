@@ -37,12 +37,13 @@ __device__ __forceinline__ int exponent_above(float maxabs) {
 // 2^4 in the digit frame and |l| <= 8, so one rounding of at most 2^-45 of
 // the scale can occur), digits 3..6 follow. Each step is exact:
 // d = rint(a), a <- 128 (a - d).
-__device__ __forceinline__ void digits7(float h, float l, int E, float d[ND]) {
+template <int N>
+__device__ __forceinline__ void digitsN(float h, float l, int E, float d[N]) {
   const float s = exp2i(7 - E);
   float a = __fmul_rn(h, s);
   float b = __fmul_rn(__fmul_rn(l, s), 2097152.0f);
 #pragma unroll
-  for (int i = 0; i < ND; ++i) {
+  for (int i = 0; i < N; ++i) {
     if (i == 3) a = __fadd_rn(a, b);
     float t = __fadd_rn(a, MAGIC);
     float di = __fsub_rn(t, MAGIC);
@@ -57,10 +58,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 // sum_g S_g 2^(-7 g) as df64 (Horner from the smallest group, TwoSum per step)
-__device__ __forceinline__ float2 combine_groups(const float S[ND]) {
-  float h = S[ND - 1], l = 0.0f;
+template <int N>
+__device__ __forceinline__ float2 combine_groups(const float S[N]) {
+  float h = S[N - 1], l = 0.0f;
 #pragma unroll
-  for (int g = ND - 2; g >= 0; --g) {
+  for (int g = N - 2; g >= 0; --g) {
     float hs = __fmul_rn(h, 0.0078125f);
     l = __fmul_rn(l, 0.0078125f);
     float2 t = two_sum(S[g], hs);
@@ -140,7 +142,7 @@ __global__ void oz_prep_rhs_kernel(int p, int p16, int nk, int K16, const double
     }
     float2 x = df_from_double(v);
     float d[ND];
-    digits7(x.x, x.y, E, d);
+    digitsN<ND>(x.x, x.y, E, d);
 #pragma unroll
     for (int i = 0; i < ND; ++i)
       Md[((size_t)i * p16 + n) * K16 + k] = __float2bfloat16_rn(d[i]);
@@ -170,8 +172,8 @@ constexpr int GM_THREADS = 256;
 __host__ __device__ inline int gm_ud_stride(int K16) { return K16 + 8; }   // bf16 elements per row
 __host__ __device__ inline int gm_md_stride(int K16) { return K16 + 8; }
 
-size_t oz_gemm_smem(int K16, int NC, int nraw) {
-  return (size_t)ND * GM_RT * gm_ud_stride(K16) * 2 + (size_t)ND * NC * gm_md_stride(K16) * 2 +
+size_t oz_gemm_smem(int K16, int NC, int nraw, int nd = ND) {
+  return (size_t)nd * GM_RT * gm_ud_stride(K16) * 2 + (size_t)nd * NC * gm_md_stride(K16) * 2 +
          (size_t)nraw * GM_RT * K16 * sizeof(float2) + (GM_RT + NC) * sizeof(int) + 64;
 }
 
@@ -188,6 +190,7 @@ __device__ __forceinline__ void gm_stage(const OzGemmArgs& a, int64_t n, int p, 
   cp_async_commit();
 }
 
+template <int NDT>
 __global__ void __launch_bounds__(GM_THREADS, 2)
 oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -196,8 +199,8 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   const int uds = gm_ud_stride(K16), mds = gm_md_stride(K16);
   const bool two = a.fuse_u1 != 0;
   __nv_bfloat16* Ud = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* Ms = Ud + (size_t)ND * GM_RT * uds;
-  float2* raw0 = reinterpret_cast<float2*>(Ms + (size_t)ND * NC * mds);
+  __nv_bfloat16* Ms = Ud + (size_t)NDT * GM_RT * uds;
+  float2* raw0 = reinterpret_cast<float2*>(Ms + (size_t)NDT * NC * mds);
   float2* raw1 = two ? raw0 + GM_RT * K16 : nullptr;
   int* Er = reinterpret_cast<int*>(raw0 + (two ? 2 : 1) * GM_RT * K16);
   int* Fs = Er + GM_RT;
@@ -206,7 +209,7 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   if ((int64_t)blockIdx.x < ntiles) gm_stage(a, n, p, K16, (int64_t)blockIdx.x * GM_RT, raw0, raw1);
 
   // right operand digits for this column slice
-  for (int e = tid; e < ND * NC * (K16 / 8); e += GM_THREADS) {
+  for (int e = tid; e < NDT * NC * (K16 / 8); e += GM_THREADS) {
     int chunk = e % (K16 / 8);
     int rowi = e / (K16 / 8);
     int plane = rowi / NC, nn = rowi - plane * NC;
@@ -240,11 +243,11 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
       __syncwarp();
       for (int cp = lane; 2 * cp < K16; cp += 32) {
         const float4 xx = *reinterpret_cast<const float4*>(row0 + 2 * cp);
-        float d0[ND], d1[ND];
-        digits7(xx.x, xx.y, E, d0);
-        digits7(xx.z, xx.w, E, d1);
+        float d0[NDT], d1[NDT];
+        digitsN<NDT>(xx.x, xx.y, E, d0);
+        digitsN<NDT>(xx.z, xx.w, E, d1);
 #pragma unroll
-        for (int i = 0; i < ND; ++i)
+        for (int i = 0; i < NDT; ++i)
           *reinterpret_cast<uint32_t*>(Ud + ((size_t)i * GM_RT + rr) * uds + 2 * cp) =
               pack_bf16x2(d0[i], d1[i]);
       }
@@ -252,9 +255,9 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     __syncthreads();  // digits ready, raw buffers free: prefetch the next tile
     if (tile + gridDim.x < ntiles) gm_stage(a, n, p, K16, (tile + gridDim.x) * GM_RT, raw0, raw1);
     // (c) tensor-core products, exact per digit-pair group
-    float acc[ND][2][4];
+    float acc[NDT][2][4];
 #pragma unroll
-    for (int g = 0; g < ND; ++g)
+    for (int g = 0; g < NDT; ++g)
 #pragma unroll
       for (int t = 0; t < 2; ++t)
 #pragma unroll
@@ -263,10 +266,10 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     const bool act0 = wc < ntl, act1 = wc + 4 < ntl;
     if (act0) {
       for (int ks = 0; ks < K16 / 16; ++ks) {
-        uint32_t A[ND][4];
+        uint32_t A[NDT][4];
         const int q = lane >> 3;
 #pragma unroll
-        for (int i = 0; i < ND; ++i)
+        for (int i = 0; i < NDT; ++i)
           ldsm_x4(A[i], Ud + ((size_t)i * GM_RT + wr * 16 + (lane & 7) + (q & 1) * 8) * uds +
                             ks * 16 + (q >> 1) * 8);
 #pragma unroll
@@ -274,12 +277,12 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
           if (t == 1 && !act1) break;
           const int nt = wc + 4 * t;
 #pragma unroll
-          for (int j = 0; j < ND; ++j) {
+          for (int j = 0; j < NDT; ++j) {
             uint32_t B[2];
             const int l16 = lane & 15;
             ldsm_x2(B, Ms + ((size_t)j * NC + nt * 8 + (l16 & 7)) * mds + ks * 16 + (l16 >> 3) * 8);
 #pragma unroll
-            for (int i = 0; i < ND - j; ++i) mma_bf16(acc[i + j][t], A[i], B);
+            for (int i = 0; i < NDT - j; ++i) mma_bf16(acc[i + j][t], A[i], B);
           }
         }
       }
@@ -298,10 +301,10 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
         float2 v[2];
 #pragma unroll
         for (int e2 = 0; e2 < 2; ++e2) {
-          float S[ND];
+          float S[NDT];
 #pragma unroll
-          for (int g = 0; g < ND; ++g) S[g] = acc[g][t][h * 2 + e2];
-          float2 w = combine_groups(S);
+          for (int g = 0; g < NDT; ++g) S[g] = acc[g][t][h * 2 + e2];
+          float2 w = combine_groups<NDT>(S);
           int sc = Er[rr] + Fs[cc + e2] - 14;
           if (sc >= -126) {
             float f = exp2i(sc);
@@ -364,8 +367,8 @@ constexpr int GR_KC = 64;
 constexpr int GR_THREADS = 512;
 constexpr int GR_STRIDE = 64 + 8;
 
-size_t oz_gram_smem() {
-  return (size_t)2 * ND * GR_KC * GR_STRIDE * 2 + (size_t)2 * GR_KC * 64 * sizeof(float2) +
+size_t oz_gram_smem(int nd = ND) {
+  return (size_t)2 * nd * GR_KC * GR_STRIDE * 2 + (size_t)2 * GR_KC * 64 * sizeof(float2) +
          (4 * 128 + 4 * 64) * sizeof(int) + 64;
 }
 
@@ -384,13 +387,14 @@ __device__ __forceinline__ void gr_stage(int64_t n, int p, int q, const float2* 
   cp_async_commit();
 }
 
+template <int NDT>
 __global__ void __launch_bounds__(GR_THREADS)
 oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
                int sym, int nbj, float2* part) {
   extern __shared__ __align__(16) unsigned char smem[];
   __nv_bfloat16* Ud = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* Vd = Ud + (size_t)ND * GR_KC * GR_STRIDE;
-  float2* rawU = reinterpret_cast<float2*>(Vd + (size_t)ND * GR_KC * GR_STRIDE);
+  __nv_bfloat16* Vd = Ud + (size_t)NDT * GR_KC * GR_STRIDE;
+  float2* rawU = reinterpret_cast<float2*>(Vd + (size_t)NDT * GR_KC * GR_STRIDE);
   float2* rawV = rawU + GR_KC * 64;
   int* cmx = reinterpret_cast<int*>(rawV + GR_KC * 64);  // [4][128] partial column maxima
   int* Eu = cmx + 4 * 128;
@@ -451,43 +455,43 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
       const float2* src = isv ? rawV : rawU;
       const float4 xx = *reinterpret_cast<const float4*>(src + r * 64 + c);
       const int* Ex = isv ? Ev : Eu;
-      float d0[ND], d1[ND];
-      digits7(xx.x, xx.y, Ex[c], d0);
-      digits7(xx.z, xx.w, Ex[c + 1], d1);
+      float d0[NDT], d1[NDT];
+      digitsN<NDT>(xx.x, xx.y, Ex[c], d0);
+      digitsN<NDT>(xx.z, xx.w, Ex[c + 1], d1);
       __nv_bfloat16* dst = isv ? Vd : Ud;
 #pragma unroll
-      for (int i = 0; i < ND; ++i)
+      for (int i = 0; i < NDT; ++i)
         *reinterpret_cast<uint32_t*>(dst + ((size_t)i * GR_KC + r) * GR_STRIDE + c) = pack_bf16x2(d0[i], d1[i]);
     }
     __syncthreads();  // digits ready, raw buffers free: prefetch the next chunk
     if (ch + gridDim.x < nchunks)
       gr_stage(n, p, q, U, V, i0, j0, (ch + gridDim.x) * GR_KC, rawU, rawV);
     if (active) {
-      float acc[ND][2][4];
+      float acc[NDT][2][4];
 #pragma unroll
-      for (int g = 0; g < ND; ++g)
+      for (int g = 0; g < NDT; ++g)
 #pragma unroll
         for (int t = 0; t < 2; ++t)
 #pragma unroll
           for (int e = 0; e < 4; ++e) acc[g][t][e] = 0.0f;
 #pragma unroll
       for (int ks = 0; ks < GR_KC / 16; ++ks) {
-        uint32_t A[ND][4];
+        uint32_t A[NDT][4];
         const int qq = lane >> 3;
 #pragma unroll
-        for (int i = 0; i < ND; ++i)
+        for (int i = 0; i < NDT; ++i)
           ldsm_x4_t(A[i], Ud + ((size_t)i * GR_KC + ks * 16 + (lane & 7) + (qq >> 1) * 8) * GR_STRIDE +
                               wi * 16 + (qq & 1) * 8);
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
 #pragma unroll
-          for (int j = 0; j < ND; ++j) {
+          for (int j = 0; j < NDT; ++j) {
             uint32_t B[2];
             const int l16 = lane & 15;
             ldsm_x2_t(B, Vd + ((size_t)j * GR_KC + ks * 16 + (l16 & 7) + (l16 >> 3) * 8) * GR_STRIDE +
                              wj * 16 + t * 8);
 #pragma unroll
-            for (int i = 0; i < ND - j; ++i) mma_bf16(acc[i + j][t], A[i], B);
+            for (int i = 0; i < NDT - j; ++i) mma_bf16(acc[i + j][t], A[i], B);
           }
         }
       }
@@ -497,10 +501,10 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
         for (int e = 0; e < 4; ++e) {
           const int ii = wi * 16 + (lane >> 2) + (e >> 1) * 8;
           const int jj = wj * 16 + t * 8 + (lane & 3) * 2 + (e & 1);
-          float S[ND];
+          float S[NDT];
 #pragma unroll
-          for (int g = 0; g < ND; ++g) S[g] = acc[g][t][e];
-          float2 w = combine_groups(S);
+          for (int g = 0; g < NDT; ++g) S[g] = acc[g][t][e];
+          float2 w = combine_groups<NDT>(S);
           int sc = Eu[ii] + Ev[jj] - 14;
           float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
           res[t][e] = df_add(res[t][e], make_float2(w.x * f1 * f2, w.y * f1 * f2));
@@ -566,24 +570,25 @@ size_t oz_rhs_bytes(int p, int nk) {
 gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const double* const M[2],
                    const double s[2], int ne, const float2* const E[2], const float2 ce[2],
                    float2* out, float2* dot_part, const float2* dot_with, bool dot_self,
-                   void* rhs_ws, cudaStream_t st, int* nparts) {
-  if (nk < 1 || nk > 2 || ne < 0 || ne > 2 || p < 1 || p > 128) return GSI_ERR_ARG;
+                   void* rhs_ws, cudaStream_t st, int* nparts, int nd) {
+  if (nk < 1 || nk > 2 || ne < 0 || ne > 2 || p < 1 || p > 128 || (nd != 3 && nd != ND))
+    return GSI_ERR_ARG;
   bool fuse = nk == 2 && M[1] == M[0] && s[0] != 0.0;
-  if (fuse && oz_gemm_smem(pad16(p), std::min(64, pad16(p)), 2) > 227 * 1024) fuse = false;
+  if (fuse && oz_gemm_smem(pad16(p), std::min(64, pad16(p)), 2, nd) > 227 * 1024) fuse = false;
   if (nk == 2 && !fuse) {
     // OUT = s0 U0 M0 + E terms, then OUT += s1 U1 M1
     const float2* U0[2] = {U[0], U[0]};
     const double* M0[2] = {M[0], M[0]};
     double s0[2] = {s[0], 0.0};
     GSI_TRY(oz_gemm(n, p, 1, U0, M0, s0, ne, E, ce, out, nullptr, nullptr, false, rhs_ws, st,
-                    nullptr));
+                    nullptr, nd));
     const float2* U1[2] = {U[1], U[1]};
     const double* M1[2] = {M[1], M[1]};
     double s1[2] = {s[1], 0.0};
     const float2* E1[2] = {out, out};
     float2 c1[2] = {make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
     return oz_gemm(n, p, 1, U1, M1, s1, 1, E1, c1, out, dot_part, dot_with, dot_self, rhs_ws, st,
-                   nparts);
+                   nparts, nd);
   }
   const int p16 = pad16(p), K16 = p16;
   const int ncs = (p16 + 63) / 64;
@@ -612,24 +617,24 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   a.dot_with = dot_with;
   a.dot_self = dot_self ? 1 : 0;
   const int NCmax = std::min(64, p16);
-  size_t smem = oz_gemm_smem(K16, NCmax, fuse ? 2 : 1);
-  GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  size_t smem = oz_gemm_smem(K16, NCmax, fuse ? 2 : 1, nd);
+  auto kern = nd == 3 ? oz_gemm_kernel<3> : oz_gemm_kernel<ND>;
+  GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int64_t ntiles = (n + GM_RT - 1) / GM_RT;
   int per_sm = 1;
-  GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oz_gemm_kernel, GM_THREADS, smem));
+  GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GM_THREADS, smem));
   per_sm = std::max(per_sm, 1);
   int gx = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * per_sm / ncs);
   gx = std::max(gx, 1);
   if (nparts) *nparts = gx * ncs;
-  oz_gemm_kernel<<<dim3(gx, ncs), GM_THREADS, smem, st>>>(n, p, p16, K16, a);
+  kern<<<dim3(gx, ncs), GM_THREADS, smem, st>>>(n, p, p16, K16, a);
   GSI_LAUNCH_CHECK();
   return GSI_OK;
 }
 
 int oz_gemm_max_parts(int p) {
   int ncs = (pad16(p) + 63) / 64;
-  return sm_count() * 2 * ncs;
+  return sm_count() * 8 * ncs;  // up to 8 resident blocks per SM for small digit counts
 }
 
 int oz_gram_blocks(int p, int q, bool sym) {
@@ -648,20 +653,40 @@ size_t oz_gram_scratch_bytes(int64_t n, int p, int q, bool sym) {
   return (size_t)oz_gram_splits(n, p, q, sym) * oz_gram_blocks(p, q, sym) * 4096 * sizeof(float2);
 }
 
+__global__ void oz_gram_reduce_df_kernel(int p, int q, int nsplit, int nbj, const float2* part,
+                                         float2* G) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)p * q) return;
+  int i = (int)(e / q), j = (int)(e - (int64_t)i * q);
+  int bi = i / 64, bj = j / 64;
+  int b = bi * nbj + bj;
+  int nblk = ((p + 63) / 64) * nbj;
+  int ii = i - bi * 64, jj = j - bj * 64;
+  float2 s = make_float2(0.f, 0.f);
+  for (int k = 0; k < nsplit; ++k) s = df_add(s, part[((size_t)k * nblk + b) * 4096 + ii * 64 + jj]);
+  G[e] = s;
+}
+
 gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bool sym, double* G,
-                   float2* scratch, cudaStream_t st) {
-  if (p < 1 || q < 1 || p > 128 || q > 128 || (sym && p != q)) return GSI_ERR_ARG;
+                   float2* scratch, cudaStream_t st, int nd, float2* Gdf) {
+  if (p < 1 || q < 1 || q > 128 || (sym && (p != q || Gdf)) || (nd != 3 && nd != ND) ||
+      (!G && !Gdf) || (p > 128 && !Gdf))
+    return GSI_ERR_ARG;
   const int nbj = (q + 63) / 64;
   const int nblk = oz_gram_blocks(p, q, sym);
   const int ns = oz_gram_splits(n, p, q, sym);
-  size_t smem = oz_gram_smem();
-  GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  size_t smem = oz_gram_smem(nd);
+  auto kern = nd == 3 ? oz_gram_kernel<3> : oz_gram_kernel<ND>;
+  GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   GSI_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)ns * nblk * 4096 * sizeof(float2), st));
-  oz_gram_kernel<<<dim3(ns, nblk), GR_THREADS, smem, st>>>(n, p, q, U, V, sym ? 1 : 0, nbj, scratch);
+  kern<<<dim3(ns, nblk), GR_THREADS, smem, st>>>(n, p, q, U, V, sym ? 1 : 0, nbj, scratch);
   GSI_LAUNCH_CHECK();
-  oz_gram_reduce_kernel<<<ceil_div(p * q, 256), 256, 0, st>>>(p, q, ns, nblk, sym ? 1 : 0, nbj,
-                                                              scratch, G);
+  if (Gdf) {
+    oz_gram_reduce_df_kernel<<<ceil_div((int64_t)p * q, 256), 256, 0, st>>>(p, q, ns, nbj, scratch, Gdf);
+  } else {
+    oz_gram_reduce_kernel<<<ceil_div(p * q, 256), 256, 0, st>>>(p, q, ns, nblk, sym ? 1 : 0, nbj,
+                                                                scratch, G);
+  }
   GSI_LAUNCH_CHECK();
   return GSI_OK;
 }

@@ -32,12 +32,16 @@ size_t oz_rhs_bytes(int p, int nk);
 gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const double* const M[2],
                    const double s[2], int ne, const float2* const E[2], const float2 ce[2],
                    float2* out, float2* dot_part, const float2* dot_with, bool dot_self,
-                   void* rhs_ws, cudaStream_t st, int* nparts);
+                   void* rhs_ws, cudaStream_t st, int* nparts, int nd = 7);
 int oz_gemm_max_parts(int p);
 size_t oz_gram_scratch_bytes(int64_t n, int p, int q, bool sym);
 // G = U^T V (float64 p x q); sym: U == V, only the upper half is computed.
+// nd: digits per operand (7: float64-class; 3: bf16-level products with exact
+// fp32 sums, used by the mixed-precision mode). With Gdf non-null the result
+// is written as df64 to Gdf (p x q, any p; q <= 128): for symmetric A this is
+// the dense apply A X = A^T X.
 gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bool sym, double* G,
-                   float2* scratch, cudaStream_t st);
+                   float2* scratch, cudaStream_t st, int nd = 7, float2* Gdf = nullptr);
 
 // df64 block helpers (df_blas.cu)
 gsi_status df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);

@@ -38,7 +38,10 @@ __host__ __device__ inline size_t sd_bytes(int p) {
          64 * (2 * sizeof(float) + 2 * sizeof(double) + 2 * sizeof(float2) + 2 * sizeof(int)) + 512;
 }
 
-__device__ SdWs sd_carve(unsigned char* base, int p) {
+// Layout: df64 matrices first, then the float32 Jacobi matrices and vectors.
+// With `split`, the df64 part lives in global memory (base) and the rest in
+// shared memory (sbase).
+__device__ SdWs sd_carve(unsigned char* base, int p, unsigned char* sbase = nullptr) {
   size_t q = (size_t)p * p;
   SdWs w;
   unsigned char* cur = base;
@@ -51,6 +54,7 @@ __device__ SdWs sd_carve(unsigned char* base, int p) {
   w.Vd = (float2*)take(q * sizeof(float2));
   w.Td = (float2*)take(q * sizeof(float2));
   w.Ud = (float2*)take(q * sizeof(float2));
+  if (sbase) cur = sbase;
   w.Af = (float*)take(q * sizeof(float));
   w.Vf = (float*)take(q * sizeof(float));
   w.al = (double*)take(p * sizeof(double));
@@ -421,7 +425,9 @@ small_df_kernel(int mode, int p, const double* C, const double* B, const double*
   __shared__ double red[SD_THREADS / 32];
   __shared__ int flag;
   __shared__ double sh_t;
-  SdWs w = sd_carve(use_smem ? sm_dyn : gws, p);
+  // use_smem: 1 = everything in shared memory, 2 = float32 part only
+  SdWs w = use_smem == 1 ? sd_carve(sm_dyn, p) : use_smem == 2 ? sd_carve(gws, p, sm_dyn)
+                                                                  : sd_carve(gws, p);
   const int q = p * p;
   long long t0 = clock64();
   eig_refined(p, B, w, red, out + 8);
@@ -496,12 +502,14 @@ gsi_status small_step_df(int mode, int p, const double* C, const double* B, cons
                          double* out, void* scratch, cudaStream_t st) {
   if (p < 1 || p > 128) return GSI_ERR_ARG;
   size_t bytes = sd_bytes(p);
-  int use_smem = bytes <= 200 * 1024 ? 1 : 0;
+  const size_t dfpart = 4 * (((size_t)p * p * sizeof(float2) + 15) & ~(size_t)15);
+  int use_smem = bytes <= 200 * 1024 ? 1 : (bytes - dfpart <= 200 * 1024 ? 2 : 0);
+  size_t sm = use_smem == 1 ? bytes : use_smem == 2 ? bytes - dfpart : 0;
   if (use_smem)
     GSI_CUDA_TRY(cudaFuncSetAttribute(small_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)bytes));
-  small_df_kernel<<<1, SD_THREADS, use_smem ? bytes : 0, st>>>(mode, p, C, B, Gam, Z, XX, XD, M, out,
-                                                               (unsigned char*)scratch, use_smem);
+                                      (int)sm));
+  small_df_kernel<<<1, SD_THREADS, sm, st>>>(mode, p, C, B, Gam, Z, XX, XD, M, out,
+                                             (unsigned char*)scratch, use_smem);
   GSI_LAUNCH_CHECK();
   return GSI_OK;
 }

@@ -97,7 +97,12 @@ struct gsi_ctx {
   int p = 0;
   gsi_opts o{};
   bool emu = true;
+  bool mixed = false;  // GSI_PREC_MIXED: 3-digit operator apply until mixed_switch
+  int nd = 7;          // digits per operand in the dense operator apply
   int fmt = GSI_CSR;
+  double* Ad = nullptr;   // dense A, float64 (GSI_DENSE)
+  float2* Adf = nullptr;  // dense A, df64
+  float2* dense_ws = nullptr;
   int64_t* rowptr = nullptr;
   int32_t* colidx = nullptr;
   double* val = nullptr;    // float64 values (native mode and Rayleigh-Ritz)
@@ -202,11 +207,21 @@ double blk_bytes(gsi_ctx* c) { return 8.0 * (double)c->n * c->p; }
 
 // ---- block operations, float64 or df64 ------------------------------------
 
-gsi_status op_matvec(gsi_ctx* c, const void* in, void* outp) {
+// accurate: an explicit Y = A X (always 7-digit); otherwise the direction's
+// apply W = A D, which the mixed mode computes with c->nd digits
+gsi_status op_matvec(gsi_ctx* c, const void* in, void* outp, bool accurate = true) {
   c->matvecs++;
   prof_begin(c);
   gsi_status s;
   double bytes;
+  if (c->fmt == GSI_DENSE) {
+    bytes = 8.0 * (double)c->n * c->n + 2 * blk_bytes(c);
+    s = c->emu ? oz_gram(c->n, (int)c->n, c->p, c->Adf, (const float2*)in, false, nullptr, c->dense_ws,
+                         c->st, accurate ? 7 : c->nd, (float2*)outp)
+               : dense_gemm(c->n, c->p, c->Ad, (const double*)in, (double*)outp, c->st);
+    prof_end(c, GSI_K_SPMM, bytes, 2.0 * (double)c->n * c->n * c->p);
+    return s;
+  }
   if (c->fmt == GSI_SELL) {
     int64_t slots = c->nchunks * c->C;
     bytes = 12.0 * (double)c->nnz + 8.0 * slots + 2 * blk_bytes(c);
@@ -347,6 +362,15 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
     if (c->res0_inf < 0.0) c->res0_inf = rinf;
     c->rel = sqrt(rr) / c->anorm;
     c->rel_inf = c->res0_inf > 0.0 ? rinf / c->res0_inf : 0.0;
+    if (c->mixed && c->nd != 7 && (c->rel <= c->o.mixed_switch || c->rel <= c->o.tol)) {
+      // correction phase: 7-digit products from here on, with an explicit AX
+      // and a fresh (gradient) direction
+      c->nd = 7;
+      GSI_TRY(op_matvec(c, c->X, c->Y));
+      c->y_fresh = true;
+      c->have_prev = false;
+      continue;
+    }
     if (c->rel <= c->o.tol || c->iters >= c->o.max_iters) {
       if (!c->y_fresh) {  // the final residual is always taken with an explicit AX
         GSI_TRY(op_matvec(c, c->X, c->Y));
@@ -381,7 +405,7 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
     Dp = c->D;
     beta_used = (c->have_prev && !restarted) ? (rr - rp) / c->rr_prev : 0.0;
   }
-  GSI_TRY(op_matvec(c, Dp, c->W));
+  GSI_TRY(op_matvec(c, Dp, c->W, false));
   GSI_TRY(op_gram(c, Dp, Dp, true, c->Bm));
   GSI_TRY(op_gram(c, Dp, c->W, true, c->Gm));
   const double* Zp = c->Bm;
@@ -565,6 +589,7 @@ gsi_status start(gsi_ctx* c, const double* X0, int on_device) {
     GSI_CUDA_TRY(cudaMemcpyAsync(c->X, X0, blk, kind, c->st));
   }
   c->iters = c->matvecs = c->restarts = c->last_evals = 0;
+  c->nd = c->mixed ? 3 : 7;
   c->y_fresh = true;
   c->have_prev = c->converged = false;
   c->rr_prev = 0.0;
@@ -597,6 +622,7 @@ gsi_status gsi_default_opts(gsi_opts* o) {
   o->cheb_lo = 0.0;
   o->cheb_hi = 0.0;
   o->cheb_scale = 0.0;
+  o->mixed_switch = 1e-5;
   return GSI_OK;
 }
 
@@ -629,9 +655,11 @@ gsi_status gsi_destroy(gsi_ctx* c) {
 
 gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t X0_on_device,
                       const gsi_opts* o, void* stream, gsi_ctx** out) {
-  if (!A || !X0 || !out || !A->rowptr || !A->colidx || !A->val) return GSI_ERR_ARG;
-  if (p < 1 || p > 128 || A->n < 2 * (int64_t)p || A->nnz < 0) return GSI_ERR_ARG;
-  if (A->fmt != GSI_CSR && A->fmt != GSI_SELL) return GSI_ERR_ARG;
+  if (!A || !X0 || !out || !A->val) return GSI_ERR_ARG;
+  if (A->fmt != GSI_CSR && A->fmt != GSI_SELL && A->fmt != GSI_DENSE) return GSI_ERR_ARG;
+  if (A->fmt != GSI_DENSE && (!A->rowptr || !A->colidx)) return GSI_ERR_ARG;
+  if (p < 1 || p > 128 || A->n < 2 * (int64_t)p || (A->fmt != GSI_DENSE && A->nnz < 0))
+    return GSI_ERR_ARG;
   gsi_opts opts;
   gsi_default_opts(&opts);
   if (o) opts = *o;
@@ -641,7 +669,8 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
   if ((opts.method != GSI_SD && opts.method != GSI_CG && opts.method != GSI_CHEB) ||
       (opts.which != 1 && opts.which != -1) ||
       opts.max_iters < 0 || !(opts.tol >= 0.0) ||
-      (opts.precision != GSI_PREC_DF64 && opts.precision != GSI_PREC_F64))
+      (opts.precision != GSI_PREC_DF64 && opts.precision != GSI_PREC_F64 &&
+       opts.precision != GSI_PREC_MIXED))
     return GSI_ERR_ARG;
   gsi_ctx* c = new gsi_ctx();
   *out = nullptr;
@@ -650,7 +679,9 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
   c->nnz = A->nnz;
   c->p = p;
   c->o = opts;
-  c->emu = opts.precision == GSI_PREC_DF64;
+  c->emu = opts.precision != GSI_PREC_F64;
+  c->mixed = opts.precision == GSI_PREC_MIXED;
+  c->nd = c->mixed ? 3 : 7;
   c->fmt = A->fmt;
   c->sign = opts.which == -1 ? -1.0 : 1.0;
   const int64_t n = c->n;
@@ -661,7 +692,26 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
     s = (expr);                 \
     if (s != GSI_OK) goto fail; \
   } while (0)
+  if (c->fmt == GSI_DENSE) c->nnz = 0;
   {
+    cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->fmt == GSI_DENSE) {
+      const size_t nn = (size_t)n * n;
+      CK(dev_alloc(c, (void**)&c->Ad, nn * sizeof(double)));
+      CK(cuda_status_ok(cudaMemcpyAsync(c->Ad, A->val, nn * sizeof(double), kind, c->st)));
+      if (c->sign < 0) {
+        scale_kernel<<<ceil_div((int64_t)nn, 256), 256, 0, c->st>>>((int64_t)nn, -1.0, c->Ad);
+        note_launch();
+        CK(cuda_status_ok(cudaGetLastError()));
+      }
+      if (c->emu) {
+        CK(dev_alloc(c, (void**)&c->Adf, nn * sizeof(float2)));
+        CK(df_from_f64((int64_t)nn, c->Ad, c->Adf, c->st));
+        CK(dev_alloc(c, (void**)&c->dense_ws, oz_gram_scratch_bytes(n, (int)n, p, false)));
+      }
+    }
+  }
+  if (c->fmt != GSI_DENSE) {
     cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(dev_alloc(c, (void**)&c->rowptr, (n + 1) * sizeof(int64_t)));
     CK(dev_alloc(c, (void**)&c->colidx, c->nnz * sizeof(int32_t)));
@@ -715,6 +765,8 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       }
       CK(cuda_status_ok(cudaStreamSynchronize(c->st)));
     }
+  }
+  {
     void* bufs[9];
     for (int i = 0; i < 9; ++i) CK(dev_alloc(c, &bufs[i], blk));
     c->X = bufs[0]; c->Y = bufs[1]; c->R = bufs[2]; c->Rp = bufs[3];
@@ -743,9 +795,13 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
     } else {
       unsigned long long* d_mx = (unsigned long long*)c->dout;
       CK(cuda_status_ok(cudaMemsetAsync(d_mx, 0, 8, c->st)));
-      csr_absmax_kernel<<<ceil_div(n, 256), 256, 0, c->st>>>(n, c->rowptr, c->val, d_mx);
-      note_launch();
-      CK(cuda_status_ok(cudaGetLastError()));
+      if (c->fmt == GSI_DENSE) {
+        CK(dense_absmax(n, c->Ad, d_mx, c->st));
+      } else {
+        csr_absmax_kernel<<<ceil_div(n, 256), 256, 0, c->st>>>(n, c->rowptr, c->val, d_mx);
+        note_launch();
+        CK(cuda_status_ok(cudaGetLastError()));
+      }
       CK(readback(c, c->dout, 1));
       c->anorm = c->host[0];
       if (!(c->anorm > 0)) c->anorm = 1.0;

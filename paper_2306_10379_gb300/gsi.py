@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(HERE, "libgsi.so")
 
 GSI_OK, GSI_ERR_ARG, GSI_ERR_CUDA, GSI_ERR_OOM, GSI_ERR_NOCONV, GSI_ERR_BREAKDOWN, \
     GSI_ERR_NONFINITE, GSI_ERR_TIMEOUT = range(8)
-GSI_CSR, GSI_SELL = 0, 1
+GSI_CSR, GSI_SELL, GSI_DENSE = 0, 1, 2
 GSI_SD, GSI_CG, GSI_CHEB = 0, 1, 2
-GSI_PREC_DF64, GSI_PREC_F64 = 0, 1
+GSI_PREC_DF64, GSI_PREC_F64, GSI_PREC_MIXED = 0, 1, 2
+PRECISIONS = {"df64": GSI_PREC_DF64, "f64": GSI_PREC_F64, "mixed": GSI_PREC_MIXED}
 KERNEL_CLASSES = ["spmm", "gram", "blockmul", "small", "reduce"]
 
 EXPORTED = [
@@ -27,7 +28,8 @@ EXPORTED = [
     "gsi_destroy", "gsi_status_str", "gsi_last_error", "gsi_spmm_csr", "gsi_sell_size",
     "gsi_csr_to_sell", "gsi_spmm_sell", "gsi_gram", "gsi_residual", "gsi_linesearch",
     "gsi_retract", "gsi_df_spmm_csr", "gsi_oz_gemm", "gsi_oz_gram", "gsi_reset",
-    "gsi_profile_enable", "gsi_profile_read", "gsi_launch_count",
+    "gsi_profile_enable", "gsi_profile_read", "gsi_launch_count", "gsi_oz_dense_apply",
+    "gsi_oz_gram_noalloc",
 ]
 
 
@@ -52,7 +54,8 @@ class Opts(ctypes.Structure):
                 ("k_restart", ctypes.c_int32), ("recompute_every", ctypes.c_int32),
                 ("explicit_ax", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("cheb_degree", ctypes.c_int32), ("cheb_lo", ctypes.c_double),
-                ("cheb_hi", ctypes.c_double), ("cheb_scale", ctypes.c_double)]
+                ("cheb_hi", ctypes.c_double), ("cheb_scale", ctypes.c_double),
+                ("mixed_switch", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -96,6 +99,7 @@ def _lib():
             "gsi_df_spmm_csr": [i64, vp, vp, vp, i32, vp, vp, vp],
             "gsi_oz_gemm": [i64, i32, i32, vp, vp, vp, vp, dbl, dbl, i32, vp, vp, vp, vp, vp],
             "gsi_oz_gram": [i64, i32, i32, vp, vp, i32, vp, vp],
+            "gsi_oz_dense_apply": [i64, i32, vp, vp, vp, i32, vp],
             "gsi_reset": [vp, vp, i32],
             "gsi_profile_enable": [vp, i32],
             "gsi_profile_read": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
@@ -277,6 +281,15 @@ def oz_gemm(U0, M0, out, s0=1.0, U1=None, M1=None, s1=0.0, E=(), c=(), stream=No
                              _dptr(out, f, (n, p, 2)), _stream(stream)), "gsi_oz_gemm")
 
 
+def oz_dense_apply(A_df, X_df, W_df, nd=7, stream=None):
+    """W = A X for symmetric dense A (df64 tensors: A (n, n, 2), X, W (n, p, 2))."""
+    import torch
+    n, p = X_df.shape[0], X_df.shape[1]
+    f = torch.float32
+    _check(lib().gsi_oz_dense_apply(n, p, _dptr(A_df, f, (n, n, 2)), _dptr(X_df, f), _dptr(W_df, f, (n, p, 2)),
+                                    int(nd), _stream(stream)), "gsi_oz_dense_apply")
+
+
 def oz_gram(U, V, G, sym=False, stream=None):
     import torch
     n, p = U.shape[0], U.shape[1]
@@ -290,6 +303,16 @@ def oz_gram(U, V, G, sym=False, stream=None):
 # Solver context
 # ----------------------------------------------------------------------------
 
+class Dense:
+    """A dense symmetric operator for Solver (val: n x n float64, numpy or CUDA tensor)."""
+
+    dense = True
+
+    def __init__(self, val):
+        self.val = val
+        self.n = int(val.shape[0])
+
+
 class Solver:
     """gsi_create / gsi_step / gsi_solve / gsi_get_basis / gsi_destroy.
 
@@ -298,12 +321,23 @@ class Solver:
 
     def __init__(self, A, p, X0, method="sd", which=1, tol=1e-8, anorm=0.0, max_iters=10000,
                  k_restart=0, recompute_every=50, explicit_ax=False, fmt="csr", precision="df64",
-                 cheb_degree=8, cheb_interval=(0.0, 0.0), cheb_scale=0.0, stream=None):
+                 cheb_degree=8, cheb_interval=(0.0, 0.0), cheb_scale=0.0, mixed_switch=1e-5,
+                 stream=None):
         import torch
         L = lib()
         self._keep = []
-        on_dev = isinstance(A.rowptr, torch.Tensor)
-        if on_dev:
+        dense = getattr(A, "dense", False)
+        on_dev = isinstance(A.val, torch.Tensor)
+        if dense:
+            if on_dev:
+                va = _dptr(A.val, torch.float64, (A.n, A.n))
+            else:
+                arr = np.ascontiguousarray(A.val, np.float64)
+                self._keep.append(arr)
+                va = ctypes.c_void_p(arr.ctypes.data)
+            rp = ci = None
+            nnz = 0
+        elif on_dev:
             rp, ci, va = _dptr(A.rowptr, torch.int64), _dptr(A.colidx, torch.int32), _dptr(A.val, torch.float64)
             nnz = int(A.colidx.numel())
         else:
@@ -312,7 +346,8 @@ class Solver:
             self._keep += arrs
             rp, ci, va = (ctypes.c_void_p(a.ctypes.data) for a in arrs)
             nnz = int(arrs[1].size)
-        m = Matrix(GSI_SELL if fmt == "sell" else GSI_CSR, int(A.n), nnz, rp, ci, va, 32, 32, 1 if on_dev else 0)
+        fm = GSI_DENSE if dense else (GSI_SELL if fmt == "sell" else GSI_CSR)
+        m = Matrix(fm, int(A.n), nnz, rp, ci, va, 32, 32, 1 if on_dev else 0)
         o = Opts()
         L.gsi_default_opts(ctypes.byref(o))
         o.method = {"sd": GSI_SD, "cg": GSI_CG, "cheb": GSI_CHEB}[method]
@@ -326,9 +361,10 @@ class Solver:
         o.k_restart = int(k_restart)
         o.recompute_every = int(recompute_every)
         o.explicit_ax = 1 if explicit_ax else 0
-        if precision not in ("df64", "f64"):
-            raise ValueError("precision must be 'df64' or 'f64'")
-        o.precision = GSI_PREC_DF64 if precision == "df64" else GSI_PREC_F64
+        if precision not in PRECISIONS:
+            raise ValueError("precision must be one of " + ", ".join(PRECISIONS))
+        o.precision = PRECISIONS[precision]
+        o.mixed_switch = float(mixed_switch)
         self.precision = precision
         if isinstance(X0, torch.Tensor):
             x0p, x0dev = _dptr(X0, torch.float64, (A.n, p)), 1
