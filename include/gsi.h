@@ -309,6 +309,91 @@ gsi_status gsi_oz_dense_apply(int64_t n, int32_t p, const float* A, const float*
 gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, const float* V,
                                int32_t sym, double* G, void* stream);
 
+/* ---- batched solver -------------------------------------------------------
+ * Many independent problems, each the dominant p_i-dimensional invariant
+ * subspace of a symmetric A_i (the problem of Sec. 2.1), iterated together
+ * by Alg. 2 (SD) or Alg. 4 (CG) with the exact line search of Alg. 3 and the
+ * recursion of Eq. (save_matvec) -- the same iteration as gsi_solve, with
+ * every decision taken on the GPU. Block data are df64; operator entries
+ * float32; the p x p step float64. The paper solves one problem at a time;
+ * batching is a GPU execution form of the same method. */
+typedef struct gsi_batch gsi_batch;
+
+/* The tile table of one pass (host-only, no GPU needed): the problems with
+ * active[i] != 0 (all when active is NULL), in the order descending p, then
+ * descending n, then ascending index, each cut into tiles of
+ *   T_i = min(tile_max, max(64, ceil(S / target_tiles)))
+ * rows (the last one ragged), S the rows of all selected problems: tiles of
+ * tile_max rows while many problems are active, finer ones when few remain.
+ * The device builds the same table at the start of every pass from the
+ * problems still active. Tile k covers rows [tile_row0[k], tile_row0[k] +
+ * tile_rows[k]) of problem tile_prob[k]. order: nprob entries or NULL;
+ * ntiles: required; the three tile arrays may be NULL, else hold capacity
+ * entries (GSI_ERR_ARG if fewer than ntiles). */
+gsi_status gsi_batched_plan(int32_t nprob, const int32_t* n, const int32_t* p, const int32_t* active,
+                            int32_t tile_max, int32_t target_tiles, int32_t* order, int32_t* ntiles,
+                            int32_t* tile_prob, int32_t* tile_row0, int32_t* tile_rows,
+                            int32_t capacity);
+
+/* Create a batch (host inputs, copied; the caller keeps ownership).
+ *   n[i], p[i]: size and block width of problem i; p[i] in {2, 4, 8, 16, 32},
+ *     n[i] >= 2 p[i].
+ *   rowptr, colidx, val: one concatenated CSR: rows of problem i are rows
+ *     n[0] + ... + n[i-1] onwards; rowptr has sum(n) + 1 non-decreasing
+ *     entries starting at 0 and indexes colidx/val globally; column indices
+ *     are local to the problem (0 <= c < n[i], checked); A_i symmetric (not
+ *     checked); values float32.
+ *   X0: concatenated row-major n[i] x p[i] float64 start blocks (need not
+ *     be orthonormal); kept for gsi_batched_reset.
+ *   anorm: NULL, or per-problem ||A_i|| for the stopping test (entries <= 0
+ *     fall back to o->anorm, then to ||A_i||_inf).
+ *   o: method GSI_SD or GSI_CG, which, tol, max_iters, k_restart,
+ *     recompute_every, explicit_ax are used; NULL = defaults.
+ * The start blocks are orthonormalised and Y = A X formed before return.
+ * Errors: GSI_ERR_ARG for invalid sizes or indices, GSI_ERR_OOM / CUDA. */
+gsi_status gsi_batched_create(int32_t nprob, const int32_t* n, const int32_t* p,
+                              const int64_t* rowptr, const int32_t* colidx, const float* val,
+                              const double* X0, const double* anorm, const gsi_opts* o,
+                              void* stream, gsi_batch** out);
+/* Tile shape: tile_max rows (32..65536), persistent CTAs per SM (1..32) of
+ * the tile kernels, tiles aimed at per CTA (1..64; target_tiles = CTAs x
+ * tiles_per_cta); restarts the batch from X0. */
+gsi_status gsi_batched_set_tiles(gsi_batch* b, int32_t tile_max, int32_t ctas_per_sm,
+                                 int32_t tiles_per_cta);
+/* Current tile shape and the persistent grid size. Outputs may be NULL. */
+gsi_status gsi_batched_get_tiles(gsi_batch* b, int32_t* tile_max, int32_t* ctas_per_sm,
+                                 int32_t* tiles_per_cta, int32_t* grid);
+/* The tile table the device built for the last pass (copied to host
+ * arrays of capacity entries; NULL arrays skipped). */
+gsi_status gsi_batched_last_plan(gsi_batch* b, int32_t* ntiles, int32_t* tile_prob,
+                                 int32_t* tile_row0, int32_t* tile_rows, int32_t capacity);
+/* Autotuner: times npasses passes from the start for every candidate tile
+ * shape (tile_max 256..4096, 2/4/8 CTAs per SM, 1/2 tiles per CTA), keeps
+ * the fastest and restarts the batch from X0. Outputs may be NULL. */
+gsi_status gsi_batched_tune(gsi_batch* b, int32_t npasses, int32_t* tile_max, int32_t* ctas_per_sm,
+                            int32_t* tiles_per_cta, double* ms_per_pass);
+/* Back to the orthonormalised X0. */
+gsi_status gsi_batched_reset(gsi_batch* b);
+/* Run npasses passes from the host (a pass is one iteration of every active
+ * problem, or the explicit AX of a problem that is about to stop). */
+gsi_status gsi_batched_step(gsi_batch* b, int32_t npasses);
+/* Run until every problem has stopped. use_graph != 0: one launch of a CUDA
+ * graph whose while-node repeats the pass until no problem is active (or
+ * 2 max_iters + 4 passes); use_graph == 0: the same passes from a host loop.
+ * passes (may be NULL): passes run. GSI_OK if every problem converged, else
+ * GSI_ERR_NOCONV (per-problem status from gsi_batched_info). */
+gsi_status gsi_batched_solve(gsi_batch* b, int32_t use_graph, int32_t* passes);
+/* Per-problem counters as gsi_info (trace = tr(X^T A X)); status: -1 while
+ * active, else GSI_OK (converged), GSI_ERR_NOCONV, GSI_ERR_BREAKDOWN or
+ * GSI_ERR_NONFINITE. Either output may be NULL. */
+gsi_status gsi_batched_info(gsi_batch* b, int32_t i, gsi_info* info, int32_t* status);
+/* Problem i's basis into host X (n[i] x p[i] row-major float64) and, if evals
+ * is not NULL, its Ritz values (p[i], descending) with X then the Ritz
+ * vectors (Eq. (rr1), explicit AX; computed for all problems at once and
+ * kept until the next pass). Either output may be NULL. */
+gsi_status gsi_batched_get_basis(gsi_batch* b, int32_t i, double* X, double* evals);
+gsi_status gsi_batched_destroy(gsi_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

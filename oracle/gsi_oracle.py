@@ -501,3 +501,48 @@ def sell_c_sigma(n, rowptr, colidx, val, C=32, sigma=32):
                     scol[slot] = max(r, 0) if r >= 0 else 0
                     sval[slot] = 0.0
     return np.array(perm, np.int64), chunk_ptr, chunk_len, scol, sval
+
+
+# ---------------------------------------------------------------------------
+# Batches of independent problems. The paper solves one problem at a time;
+# a batch is just that method applied to each problem (Sec. 2.1 problem
+# statement per A_i), and the GPU's work tables are plain integer
+# bookkeeping with the definition written out here.
+# ---------------------------------------------------------------------------
+
+def batched_plan(n, p, tile_max, target_tiles, active=None):
+    """Problem order (descending p, then descending n, then ascending index)
+    and the tile table of one pass over the problems with active[i] (all
+    when active is None): with S their total rows and T = ceil(S /
+    target_tiles), problem i is cut into tiles of
+    T_i = min(tile_max, max(64, T)) consecutive rows, the last
+    one ragged. Returns (order, tiles), tiles a list of (problem, first row,
+    rows)."""
+    order = sorted(range(len(n)), key=lambda i: (-int(p[i]), -int(n[i]), i))
+    on = [True] * len(n) if active is None else [bool(a) for a in active]
+    S = sum(int(n[i]) for i in range(len(n)) if on[i])
+    T = -(-S // int(target_tiles)) if S > 0 else 1
+    tiles = []
+    for i in order:
+        if not on[i]:
+            continue
+        Ti = min(int(tile_max), max(64, T))
+        r = 0
+        while r < int(n[i]):
+            tiles.append((i, r, min(Ti, int(n[i]) - r)))
+            r += Ti
+    return order, tiles
+
+
+def batched_solve(mats, X0s, opts: Options, anorms=None, callback=None):
+    """solve() on every problem of a batch, independently. mats[i] is a
+    scipy sparse matrix, X0s[i] its start block; anorms[i] (optional) the
+    norm of the stopping test. callback(i, k, X, Y, t) as in solve()."""
+    out = []
+    for i, (A, X0) in enumerate(zip(mats, X0s)):
+        o = Options(**{**opts.__dict__})
+        if anorms is not None:
+            o.anorm = float(anorms[i])
+        cb = None if callback is None else (lambda k, X, Y, t, i=i: callback(i, k, X, Y, t))
+        out.append(solve(A, X0, o, callback=cb))
+    return out

@@ -101,6 +101,21 @@ def _lib():
             "gsi_oz_gram": [i64, i32, i32, vp, vp, i32, vp, vp],
             "gsi_oz_dense_apply": [i64, i32, vp, vp, vp, i32, vp],
             "gsi_reset": [vp, vp, i32],
+            "gsi_batched_plan": [i32, vp, vp, vp, i32, i32, vp, ctypes.POINTER(i32), vp, vp, vp, i32],
+            "gsi_batched_create": [i32, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts), vp,
+                                   ctypes.POINTER(vp)],
+            "gsi_batched_set_tiles": [vp, i32, i32, i32],
+            "gsi_batched_get_tiles": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32)],
+            "gsi_batched_last_plan": [vp, ctypes.POINTER(i32), vp, vp, vp, i32],
+            "gsi_batched_tune": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                 ctypes.POINTER(dbl)],
+            "gsi_batched_reset": [vp],
+            "gsi_batched_step": [vp, i32],
+            "gsi_batched_solve": [vp, i32, ctypes.POINTER(i32)],
+            "gsi_batched_info": [vp, i32, ctypes.POINTER(Info), ctypes.POINTER(i32)],
+            "gsi_batched_get_basis": [vp, i32, vp, vp],
+            "gsi_batched_destroy": [vp],
             "gsi_profile_enable": [vp, i32],
             "gsi_profile_read": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
                                  ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
@@ -460,3 +475,137 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def batched_plan(n, p, tile_max, target_tiles, active=None):
+    """Host-only tile table of one pass of the batched solver:
+    (order, [(problem, first row, rows), ...])."""
+    L = lib()
+    n = np.ascontiguousarray(n, np.int32)
+    p = np.ascontiguousarray(p, np.int32)
+    act = None if active is None else np.ascontiguousarray(active, np.int32)
+    ap = None if act is None else act.ctypes.data
+    nt = ctypes.c_int32()
+    order = np.zeros(n.size, np.int32)
+    _check(L.gsi_batched_plan(n.size, n.ctypes.data, p.ctypes.data, ap, int(tile_max), int(target_tiles),
+                              order.ctypes.data, ctypes.byref(nt), None, None, None, 0), "gsi_batched_plan")
+    cap = nt.value
+    tp, t0, tr = (np.zeros(max(cap, 1), np.int32) for _ in range(3))
+    _check(L.gsi_batched_plan(n.size, n.ctypes.data, p.ctypes.data, ap, int(tile_max), int(target_tiles),
+                              None, ctypes.byref(nt), tp.ctypes.data, t0.ctypes.data, tr.ctypes.data, cap),
+           "gsi_batched_plan")
+    return order, list(zip(tp[:cap].tolist(), t0[:cap].tolist(), tr[:cap].tolist()))
+
+
+class Batch:
+    """gsi_batched_create / _tune / _step / _solve / _info / _get_basis.
+
+    B: object with n, p (per problem), rowptr (global int64), colidx (local
+    int32), val (float32) and X0 (concatenated float64 start blocks), as
+    made by inputs.er_batch."""
+
+    def __init__(self, B, method="cg", which=1, tol=1e-8, anorm=None, max_iters=10000,
+                 k_restart=0, recompute_every=50, explicit_ax=False, stream=None):
+        L = lib()
+        self._keep = [np.ascontiguousarray(B.n, np.int32), np.ascontiguousarray(B.p, np.int32),
+                      np.ascontiguousarray(B.rowptr, np.int64), np.ascontiguousarray(B.colidx, np.int32),
+                      np.ascontiguousarray(B.val, np.float32), np.ascontiguousarray(B.X0, np.float64)]
+        an = None
+        if anorm is not None:
+            an = np.ascontiguousarray(anorm, np.float64)
+            self._keep.append(an)
+        o = Opts()
+        L.gsi_default_opts(ctypes.byref(o))
+        o.method = {"sd": GSI_SD, "cg": GSI_CG}[method]
+        o.which = int(which)
+        o.tol = float(tol)
+        o.max_iters = int(max_iters)
+        o.k_restart = int(k_restart)
+        o.recompute_every = int(recompute_every)
+        o.explicit_ax = 1 if explicit_ax else 0
+        self.n = self._keep[0].copy()
+        self.p = self._keep[1].copy()
+        self.nprob = int(self.n.size)
+        self._stream = stream
+        ctx = ctypes.c_void_p()
+        _check(L.gsi_batched_create(self.nprob, *(a.ctypes.data for a in self._keep[:6]),
+                                    None if an is None else an.ctypes.data, ctypes.byref(o),
+                                    _stream(stream), ctypes.byref(ctx)), "gsi_batched_create")
+        self._ctx = ctx
+
+    def set_tiles(self, tile_max, ctas_per_sm, tiles_per_cta=2):
+        _check(lib().gsi_batched_set_tiles(self._ctx, int(tile_max), int(ctas_per_sm), int(tiles_per_cta)),
+               "gsi_batched_set_tiles")
+
+    def tiles(self):
+        a, b, c, d = (ctypes.c_int32() for _ in range(4))
+        _check(lib().gsi_batched_get_tiles(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                           ctypes.byref(d)), "gsi_batched_get_tiles")
+        return {"tile_max": a.value, "ctas_per_sm": b.value, "tiles_per_cta": c.value, "grid": d.value}
+
+    def last_plan(self):
+        """The tile table the device built for the last pass."""
+        nt = ctypes.c_int32()
+        _check(lib().gsi_batched_last_plan(self._ctx, ctypes.byref(nt), None, None, None, 0),
+               "gsi_batched_last_plan")
+        cap = max(nt.value, 1)
+        tp, t0, tr = (np.zeros(cap, np.int32) for _ in range(3))
+        _check(lib().gsi_batched_last_plan(self._ctx, ctypes.byref(nt), tp.ctypes.data, t0.ctypes.data,
+                                           tr.ctypes.data, cap), "gsi_batched_last_plan")
+        k = nt.value
+        return list(zip(tp[:k].tolist(), t0[:k].tolist(), tr[:k].tolist()))
+
+    def tune(self, npasses=3):
+        a, b, c, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().gsi_batched_tune(self._ctx, int(npasses), ctypes.byref(a), ctypes.byref(b),
+                                      ctypes.byref(c), ctypes.byref(ms)), "gsi_batched_tune")
+        return {"tile_max": a.value, "ctas_per_sm": b.value, "tiles_per_cta": c.value,
+                "ms_per_pass": ms.value}
+
+    def reset(self):
+        _check(lib().gsi_batched_reset(self._ctx), "gsi_batched_reset")
+
+    def step(self, npasses=1):
+        _check(lib().gsi_batched_step(self._ctx, int(npasses)), "gsi_batched_step")
+
+    def solve(self, use_graph=True, check=True):
+        """Run to the end; returns the number of passes. check=False keeps a
+        GSI_ERR_NOCONV (some problem not converged) silent."""
+        passes = ctypes.c_int32()
+        st = lib().gsi_batched_solve(self._ctx, 1 if use_graph else 0, ctypes.byref(passes))
+        if check or st != GSI_ERR_NOCONV:
+            _check(st, "gsi_batched_solve")
+        return passes.value
+
+    def info(self, i):
+        inf, st = Info(), ctypes.c_int32()
+        _check(lib().gsi_batched_info(self._ctx, int(i), ctypes.byref(inf), ctypes.byref(st)),
+               "gsi_batched_info")
+        d = {k: getattr(inf, k) for k, _ in Info._fields_}
+        d["status"] = st.value
+        return d
+
+    def basis(self, i, evals=True):
+        X = np.zeros((int(self.n[i]), int(self.p[i])), np.float64)
+        ev = np.zeros(int(self.p[i]), np.float64) if evals else None
+        _check(lib().gsi_batched_get_basis(self._ctx, int(i), X.ctypes.data,
+                                           None if ev is None else ev.ctypes.data),
+               "gsi_batched_get_basis")
+        return X, ev
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().gsi_batched_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

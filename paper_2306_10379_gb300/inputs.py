@@ -156,8 +156,9 @@ def fd_laplacian(dims) -> CSR:
 def er_laplacian(n: int, seed: int, mean_degree: int = 8) -> CSR:
     """Graph Laplacian D - W of an Erdos-Renyi G(n, M) graph, M = n*mean_degree/2
     distinct undirected unit-weight edges drawn in Philox order (self-loops and
-    repeats rejected), plus a diagonal shift U(0,1) rounded to float32 so that
-    every entry is exactly representable in float32."""
+    repeats rejected), plus a diagonal shift U(0,1); each diagonal entry
+    degree + shift is rounded to float32, so that every entry is exactly
+    representable in float32."""
     m_target = n * mean_degree // 2
     keys = np.empty(0, dtype=np.int64)
     chunk = int(m_target * 1.25) + 64
@@ -175,11 +176,12 @@ def er_laplacian(n: int, seed: int, mean_degree: int = 8) -> CSR:
         stream += 1
     keys = keys[:m_target]
     lo, hi = keys // n, keys % n
-    shift = uniform53(n, seed, stream=1).astype(np.float32).astype(np.float64)
+    shift = uniform53(n, seed, stream=1)
     rows = np.concatenate([lo, hi, np.arange(n)])
     cols = np.concatenate([hi, lo, np.arange(n)])
     deg = np.bincount(lo, minlength=n) + np.bincount(hi, minlength=n)
-    vals = np.concatenate([-np.ones(2 * m_target), deg + shift])
+    diag = (deg + shift).astype(np.float32).astype(np.float64)
+    vals = np.concatenate([-np.ones(2 * m_target), diag])
     order = np.lexsort((cols, rows))
     rows, cols, vals = rows[order], cols[order], vals[order]
     rowptr = np.zeros(n + 1, dtype=np.int64)
@@ -254,3 +256,50 @@ def laplacian_eigenvalues(dims) -> np.ndarray:
         s = 4.0 * np.sin(k * np.pi / (2.0 * (d + 1))) ** 2
         total = (total[:, None] + s[None, :]).ravel()
     return np.sort(total)[::-1]
+
+
+class ERBatch:
+    """A batch of Erdos-Renyi graph Laplacians with their start blocks.
+
+    mats[i] is problem i's CSR (float64 values, each exactly a float32);
+    rowptr/colidx/val is the concatenated CSR of the batched solver (rowptr
+    global, column indices local to the problem, values float32); X0 the
+    concatenated row-major start blocks."""
+
+    def __init__(self, n, p, mats, X0s):
+        self.n = np.asarray(n, dtype=np.int32)
+        self.p = np.asarray(p, dtype=np.int32)
+        self.mats = mats
+        self.X0s = X0s
+        nnz = np.array([m.rowptr[-1] for m in mats], dtype=np.int64)
+        base = np.concatenate([[0], np.cumsum(nnz)[:-1]])
+        self.rowptr = np.concatenate([[0]] + [m.rowptr[1:] + b for m, b in zip(mats, base)]).astype(np.int64)
+        self.colidx = np.concatenate([m.colidx for m in mats]).astype(np.int32)
+        self.val = np.concatenate([m.val for m in mats]).astype(np.float32)
+        self.X0 = np.concatenate([x.ravel() for x in X0s]).astype(np.float64)
+
+    @property
+    def nprob(self) -> int:
+        return int(self.n.size)
+
+
+def batched_sizes(nprob: int, seed: int, n_lo: int = 2048, n_hi: int = 65536,
+                  p_choices=(4, 8, 16, 32)):
+    """n_i uniform on the integers [n_lo, n_hi] and p_i uniform over p_choices
+    (Philox stream 4 of `seed`)."""
+    u = uniform53(2 * nprob, seed, stream=4)
+    n = n_lo + np.floor(u[0::2] * (n_hi - n_lo + 1)).astype(np.int64)
+    p = np.asarray(p_choices, dtype=np.int64)[np.floor(u[1::2] * len(p_choices)).astype(np.int64)]
+    return n.astype(np.int32), p.astype(np.int32)
+
+
+def er_batch(nprob: int, seed: int, n_lo: int = 2048, n_hi: int = 65536,
+             p_choices=(4, 8, 16, 32), sizes=None) -> ERBatch:
+    """Problem i: er_laplacian(n_i, seed + 1 + i) (mean degree 8, diagonal
+    shift U(0,1) rounded to float32) and start block
+    start_block(n_i, p_i, seed + 1_000_003 + i). `sizes` = (n, p) overrides
+    the drawn sizes."""
+    n, p = sizes if sizes is not None else batched_sizes(nprob, seed, n_lo, n_hi, p_choices)
+    mats = [er_laplacian(int(n[i]), seed + 1 + i) for i in range(len(n))]
+    X0s = [start_block(int(n[i]), int(p[i]), seed + 1_000_003 + i) for i in range(len(n))]
+    return ERBatch(n, p, mats, X0s)

@@ -25,3 +25,13 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def torch_cuda():
+    """torch with a CUDA device, after building libgsi.so in-tree."""
+    import torch
+    from paper_2306_10379_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return torch

@@ -19,13 +19,6 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12
 
 
-@pytest.fixture(scope="module")
-def torch_cuda():
-    import torch
-    from paper_2306_10379_gb300 import build
-    build.build()
-    assert torch.cuda.is_available()
-    return torch
 
 
 def _dev(torch, a, dtype=None):

@@ -103,8 +103,9 @@ def test_er_laplacian_structure():
     assert off.nnz == 2 * 4 * 3000                  # M = 4n distinct undirected edges
     rows = np.asarray(abs(off).sum(axis=1)).ravel()
     shift = D.diagonal() - rows
-    assert np.all((shift >= 0) & (shift < 1))
-    assert np.all(shift.astype(np.float32).astype(np.float64) == shift)
+    assert np.all((shift >= 0) & (shift <= 1))
+    # every entry (degree + shift on the diagonal) is exactly a float32
+    assert np.all(A.val.astype(np.float32).astype(np.float64) == A.val)
 
 
 # ---------------------------------------------------------- line search
