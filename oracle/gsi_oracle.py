@@ -546,3 +546,115 @@ def batched_solve(mats, X0s, opts: Options, anorms=None, callback=None):
         cb = None if callback is None else (lambda k, X, Y, t, i=i: callback(i, k, X, Y, t))
         out.append(solve(A, X0, o, callback=cb))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Learned warm start. The paper motivates warm starts from related problems
+# (Sec. 1, subspace iteration reused across a sequence of operators) but
+# prints no network; what follows is the plain definition of each piece:
+# a coarse basis C (m x p on an nc x nc grid) mapped to the fine grid by
+# bilinear prolongation P, a multilayer perceptron producing C from the 16
+# field coefficients, the subspace loss of span(P C) against the plain
+# method's converged basis U, its gradient, and the Adam update.
+# ---------------------------------------------------------------------------
+
+def prolongation_1d(nc, nf):
+    """P1 (nf x nc): hat-function interpolation from nc interior coarse nodes
+    at (a+1)/(nc+1) to nf interior fine nodes at (i+1)/(nf+1) on [0, 1] with
+    zero boundary values."""
+    xf = (np.arange(nf) + 1.0) / (nf + 1)
+    xc = (np.arange(nc) + 1.0) / (nc + 1)
+    return np.maximum(0.0, 1.0 - np.abs(xf[:, None] - xc[None, :]) * (nc + 1))
+
+
+def prolongation(nc, nf):
+    """Bilinear prolongation P = P1 (x) P1 (nf^2 x nc^2, scipy CSR), fine node
+    (i, j) at row i + nf j, coarse node (a, b) at column a + nc b (the
+    ordering of the 5-point operators)."""
+    P1 = sp.csr_matrix(prolongation_1d(nc, nf))
+    return sp.kron(P1, P1, format="csr")
+
+
+def bf16_round(x):
+    """float32(x) rounded to bfloat16 (nearest, ties to even), as float64."""
+    f = np.ascontiguousarray(np.asarray(x, np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mlp_init(din, hidden, dout, seed):
+    """He-style initial weights from the shared Philox normals: W ~ N(0, 2/fan_in)
+    (last layer N(0, 1/fan_in)), zero biases. Returns a dict of float32 arrays."""
+    from paper_2306_10379_gb300.inputs import gaussian
+    sizes = [("W1", hidden, din, 2.0), ("W2", hidden, hidden, 2.0), ("W3", dout, hidden, 1.0)]
+    prm = {}
+    for k, (name, r, c, g) in enumerate(sizes):
+        prm[name] = (gaussian(r * c, seed, stream=20 + k).reshape(r, c) * np.sqrt(g / c)).astype(np.float32)
+    prm["b1"] = np.zeros(hidden, np.float32)
+    prm["b2"] = np.zeros(hidden, np.float32)
+    prm["b3"] = np.zeros(dout, np.float32)
+    return prm
+
+
+def mlp_forward(prm, x, bf16=True):
+    """out = W3 r(W2 r(W1 x + b1) + b2) + b3 for a batch x (B x din), r = ReLU.
+    With bf16, every product's operands are rounded to bfloat16 (weights and
+    the layer inputs); sums and biases in float64. Returns (out, cache)."""
+    q = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
+    a0 = q(x)
+    z1 = a0 @ q(prm["W1"]).T + prm["b1"]
+    h1 = np.maximum(z1, 0.0)
+    a1 = q(h1)
+    z2 = a1 @ q(prm["W2"]).T + prm["b2"]
+    h2 = np.maximum(z2, 0.0)
+    a2 = q(h2)
+    out = a2 @ q(prm["W3"]).T + prm["b3"]
+    return out, (a0, z1, a1, z2, a2)
+
+
+def mlp_backward(prm, cache, dout, bf16=True):
+    """Gradients of sum(out * dout) w.r.t. the parameters (backpropagation
+    through the three layers; with bf16 the products' operands -- the
+    incoming gradient, weights and layer inputs -- rounded to bfloat16)."""
+    q = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
+    a0, z1, a1, z2, a2 = cache
+    g3 = q(dout)
+    grads = {"W3": g3.T @ a2, "b3": np.asarray(dout, np.float64).sum(0)}
+    d2 = (g3 @ q(prm["W3"])) * (z2 > 0)
+    g2 = q(d2)
+    grads["W2"] = g2.T @ a1
+    grads["b2"] = d2.sum(0)
+    d1 = (g2 @ q(prm["W2"])) * (z1 > 0)
+    g1 = q(d1)
+    grads["W1"] = g1.T @ a0
+    grads["b1"] = d1.sum(0)
+    return grads
+
+
+def warm_loss_grad(C, S, Bt):
+    """Subspace loss of one sample and its gradient w.r.t. the coarse basis C
+    (m x p): with X = P C, N = X^T X = C^T S C (S = P^T P), Bt = P^T U (U the
+    plain method's orthonormal n x p basis), Q = C^T Bt Bt^T C,
+        L = p - tr(N^{-1} Q) = sum of sin^2 of the principal angles between
+            span(X) and span(U),
+        dL/dC = -2 [Bt (Bt^T C) N^{-1} - S C N^{-1} Q N^{-1}]."""
+    C = np.asarray(C, np.float64)
+    p = C.shape[1]
+    SC = S @ C
+    N = C.T @ SC
+    G = Bt.T @ C
+    Q = G.T @ G
+    Ni = np.linalg.inv(N)
+    L = p - float(np.trace(Ni @ Q))
+    dC = -2.0 * (Bt @ (G @ Ni) - SC @ (Ni @ Q @ Ni))
+    return L, dC
+
+
+def adam_step(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015) at step t >= 1; returns (w, m, v)."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v

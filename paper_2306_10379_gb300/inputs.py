@@ -194,9 +194,11 @@ def diffusion_coefficients(seed: int) -> np.ndarray:
     return gaussian(16, seed, stream=3).reshape(4, 4)
 
 
-def diffusion_fd(nx: int, xi: np.ndarray, corr_len: float = 0.1) -> CSR:
+def diffusion_fd(nx: int, xi: np.ndarray, corr_len: float = 0.1, f32: bool = False) -> CSR:
     """5-point FD of -div(kappa grad u) on the unit square, nx*nx interior points,
-    Dirichlet boundary, h = 1/(nx+1), unscaled by h^2.
+    Dirichlet boundary, h = 1/(nx+1), unscaled by h^2. With f32, the face
+    coefficients are rounded to float32 first, so that every entry (the
+    diagonal summed in float32) is exactly a float32 and A stays symmetric.
 
     log kappa(x, y) = sum_ab xi_ab w_ab cos(pi a x) cos(pi b y),
     w_ab = exp(-pi^2 l^2 (a^2 + b^2) / 4). Face coefficients are harmonic means
@@ -213,9 +215,15 @@ def diffusion_fd(nx: int, xi: np.ndarray, corr_len: float = 0.1) -> CSR:
     n = nx * nx
     I, J = np.meshgrid(np.arange(1, nx + 1), np.arange(1, nx + 1), indexing="ij")
     I, J = I.T.ravel(), J.T.ravel()                   # row r = (i-1) + nx*(j-1)
+    if f32:
+        kx = kx.astype(np.float32).astype(np.float64)
+        ky = ky.astype(np.float32).astype(np.float64)
     west, east = kx[I - 1, J], kx[I, J]
     south, north = ky[I, J - 1], ky[I, J]
     diag = west + east + south + north
+    if f32:
+        diag = (((west.astype(np.float32) + east.astype(np.float32)) + south.astype(np.float32))
+                + north.astype(np.float32)).astype(np.float64)
     r = np.arange(n)
     entries = [(r - nx, -south, J > 1), (r - 1, -west, I > 1), (r, diag, np.ones(n, bool)),
                (r + 1, -east, I < nx), (r + nx, -north, J < nx)]
@@ -303,3 +311,15 @@ def er_batch(nprob: int, seed: int, n_lo: int = 2048, n_hi: int = 65536,
     mats = [er_laplacian(int(n[i]), seed + 1 + i) for i in range(len(n))]
     X0s = [start_block(int(n[i]), int(p[i]), seed + 1_000_003 + i) for i in range(len(n))]
     return ERBatch(n, p, mats, X0s)
+
+
+def diffusion_batch(nops: int, seed: int, nx: int, p: int) -> tuple:
+    """Operators i = 0..nops-1 of the diffusion family on an nx x nx grid:
+    coefficients diffusion_coefficients(seed + i) (the 16 network inputs),
+    float32-exact 5-point operators, start blocks
+    start_block(nx^2, p, seed + 2_000_003 + i). Returns (ERBatch, params
+    (nops x 16))."""
+    xis = [diffusion_coefficients(seed + i) for i in range(nops)]
+    mats = [diffusion_fd(nx, xi, f32=True) for xi in xis]
+    X0s = [start_block(nx * nx, p, seed + 2_000_003 + i) for i in range(nops)]
+    return ERBatch([nx * nx] * nops, [p] * nops, mats, X0s), np.stack([x.ravel() for x in xis])
