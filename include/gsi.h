@@ -394,6 +394,71 @@ gsi_status gsi_batched_info(gsi_batch* b, int32_t i, gsi_info* info, int32_t* st
 gsi_status gsi_batched_get_basis(gsi_batch* b, int32_t i, double* X, double* evals);
 gsi_status gsi_batched_destroy(gsi_batch* b);
 
+/* New start blocks (concatenated as in gsi_batched_create; host or device
+ * float64 by on_device), kept as the batch's X0; orthonormalised, Y = A X. */
+gsi_status gsi_batched_restart(gsi_batch* b, const double* X0, int32_t on_device);
+
+/* ---- learned warm start ----------------------------------------------------
+ * A multilayer perceptron din -> hidden -> hidden -> dout (ReLU, ReLU,
+ * linear) maps the coefficients of an operator of a family to a coarse basis
+ * C (m x p, dout = m p, row-major); the start block is its prolongation
+ * P C. The paper motivates warm starts from related problems (Sec. 1) but
+ * prints no network: these entry points are the project's. All pointers
+ * below are device pointers unless stated; work is ordered on `stream`. */
+typedef struct gsi_mlp gsi_mlp;
+
+/* Parameters in one float32 vector: W1 (hidden x din), b1, W2 (hidden x
+ * hidden), b2, W3 (dout x hidden), b3, row-major. */
+int64_t gsi_mlp_num_params(int32_t din, int32_t hidden, int32_t dout);
+/* params: host float32, copied. max_batch: largest batch of later calls. */
+gsi_status gsi_mlp_create(int32_t din, int32_t hidden, int32_t dout, int32_t max_batch,
+                          const float* params, void* stream, gsi_mlp** out);
+/* Current parameters and last gradients into host arrays (either NULL). */
+gsi_status gsi_mlp_get_params(gsi_mlp* n, float* params, float* grads);
+/* out (batch x dout) = MLP(x (batch x din)); products on the tensor cores
+ * with bfloat16 operands and float32 sums; keeps the activations for the
+ * next gsi_mlp_backward. */
+gsi_status gsi_mlp_forward(gsi_mlp* n, int32_t batch, const float* x, float* out);
+/* Gradients of sum(out * dout) for the last forward's batch (same x),
+ * stored in the context (overwritten). */
+gsi_status gsi_mlp_backward(gsi_mlp* n, int32_t batch, const float* x, const float* dout);
+/* One Adam step (Kingma & Ba 2015) with the stored gradients. */
+gsi_status gsi_mlp_adam(gsi_mlp* n, double lr, double beta1, double beta2, double eps);
+/* Per sample s of a batch: C = C[s], Bt = Bt[s] (m x p float32, consecutive
+ * samples m p apart), S = P^T P (m x m CSR, float64 values): N = C^T S C,
+ * Q = C^T Bt Bt^T C, loss[s] = p - tr(N^{-1} Q) (the sum of sin^2 of the
+ * principal angles between span(P C) and span(U) when Bt = P^T U, U
+ * orthonormal), dC[s] = gscale * dloss/dC = -2 gscale [Bt Bt^T C N^{-1} -
+ * S C N^{-1} Q N^{-1}]. SC_scratch: batch m p floats. loss float64; NaN
+ * (and dC = 0) where N is not positive definite. p <= 64. */
+gsi_status gsi_warm_loss_grad(int32_t batch, int32_t m, int32_t p, const int64_t* S_rowptr,
+                              const int32_t* S_colidx, const double* S_val, const float* C,
+                              const float* Bt, float* SC_scratch, double* loss, float* dC, float gscale,
+                              void* stream);
+/* forward, mean loss gradient over the batch, backward, Adam (0.9, 0.999,
+ * 1e-8); mean_loss (host, may be NULL) is the batch's mean loss before the
+ * step. dout of the network must equal m p. */
+gsi_status gsi_warm_train_step(gsi_mlp* n, int32_t batch, const float* x, int32_t m, int32_t p,
+                               const int64_t* S_rowptr, const int32_t* S_colidx, const double* S_val,
+                               const float* Bt, double lr, double* mean_loss);
+/* X[s] = P C[s]: bilinear prolongation from nc x nc interior coarse nodes
+ * at (a+1)/(nc+1) to nf x nf fine nodes at (i+1)/(nf+1) of the unit square
+ * with zero boundary values; node (i, j) is row i + nf j. C float32
+ * (batch x nc^2 x p), X float64 (batch x nf^2 x p). */
+gsi_status gsi_prolong(int32_t nc, int32_t nf, int32_t p, int32_t batch, const float* C, double* X,
+                       void* stream);
+/* Bt[s] = P^T U[s] (the transpose of gsi_prolong): U float64, Bt float32. */
+gsi_status gsi_restrict(int32_t nc, int32_t nf, int32_t p, int32_t batch, const double* U, float* Bt,
+                        void* stream);
+/* C = alpha op(A) op(B) + beta C (+ bias[j]), then C = 0 where
+ * mask[i][j] <= 0 (mask may be NULL), then ReLU if relu: A(i,k) =
+ * A[i sai + k sak], B(k,j) = B[k sbk + j sbj], C[i ldc + j]; float32 in
+ * and out, operands rounded to bfloat16, float32 sums (tensor cores). */
+gsi_status gsi_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, int64_t sai, int64_t sak,
+                         const float* B, int64_t sbk, int64_t sbj, float* C, int64_t ldc, float alpha,
+                         float beta, const float* bias, const float* mask, int32_t relu, void* stream);
+gsi_status gsi_mlp_destroy(gsi_mlp* n);
+
 #ifdef __cplusplus
 }
 #endif

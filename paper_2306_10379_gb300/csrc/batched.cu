@@ -1536,3 +1536,12 @@ gsi_status gsi_batched_get_basis(gsi_batch* b, int32_t i, double* X, double* eva
 }
 
 }  // extern "C"
+
+extern "C" gsi_status gsi_batched_restart(gsi_batch* b, const double* X0, int32_t on_device) {
+  if (!b || !X0) return GSI_ERR_ARG;
+  GSI_CUDA_TRY(cudaMemcpyAsync(b->X0, X0, (size_t)b->elems * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->st));
+  GSI_TRY(start(b));
+  GSI_CUDA_TRY(cudaStreamSynchronize(b->st));
+  return GSI_OK;
+}

@@ -116,6 +116,19 @@ def _lib():
             "gsi_batched_info": [vp, i32, ctypes.POINTER(Info), ctypes.POINTER(i32)],
             "gsi_batched_get_basis": [vp, i32, vp, vp],
             "gsi_batched_destroy": [vp],
+            "gsi_batched_restart": [vp, vp, i32],
+            "gsi_mlp_create": [i32, i32, i32, i32, vp, vp, ctypes.POINTER(vp)],
+            "gsi_mlp_get_params": [vp, vp, vp],
+            "gsi_mlp_forward": [vp, i32, vp, vp],
+            "gsi_mlp_backward": [vp, i32, vp, vp],
+            "gsi_mlp_adam": [vp, dbl, dbl, dbl, dbl],
+            "gsi_mlp_destroy": [vp],
+            "gsi_warm_loss_grad": [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_float, vp],
+            "gsi_warm_train_step": [vp, i32, vp, i32, i32, vp, vp, vp, vp, dbl, ctypes.POINTER(dbl)],
+            "gsi_prolong": [i32, i32, i32, i32, vp, vp, vp],
+            "gsi_restrict": [i32, i32, i32, i32, vp, vp, vp],
+            "gsi_gemm_bf16": [i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, ctypes.c_float,
+                              ctypes.c_float, vp, vp, i32, vp],
             "gsi_profile_enable": [vp, i32],
             "gsi_profile_read": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
                                  ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
@@ -130,6 +143,8 @@ def _lib():
         L.gsi_last_error.restype = ctypes.c_char_p
         L.gsi_launch_count.argtypes = []
         L.gsi_launch_count.restype = ctypes.c_int64
+        L.gsi_mlp_num_params.argtypes = [i32, i32, i32]
+        L.gsi_mlp_num_params.restype = ctypes.c_int64
         _LIB = L
     return _LIB
 
@@ -593,6 +608,15 @@ class Batch:
                "gsi_batched_get_basis")
         return X, ev
 
+    def restart(self, X0):
+        """New start blocks (concatenated float64, numpy or torch CUDA)."""
+        import torch
+        if isinstance(X0, torch.Tensor):
+            _check(lib().gsi_batched_restart(self._ctx, _dptr(X0, torch.float64), 1), "gsi_batched_restart")
+        else:
+            X0 = np.ascontiguousarray(X0, np.float64)
+            _check(lib().gsi_batched_restart(self._ctx, X0.ctypes.data, 0), "gsi_batched_restart")
+
     def close(self):
         if getattr(self, "_ctx", None):
             lib().gsi_batched_destroy(self._ctx)
@@ -609,3 +633,133 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- learned warm start --------------------------------------------------------
+
+def mlp_num_params(din, hidden, dout):
+    return int(lib().gsi_mlp_num_params(int(din), int(hidden), int(dout)))
+
+
+def _f32(t):
+    import torch
+    return _dptr(t, torch.float32)
+
+
+class MLP:
+    """gsi_mlp_*: din -> hidden -> hidden -> dout, parameters as one float32
+    vector W1, b1, W2, b2, W3, b3 (row-major)."""
+
+    def __init__(self, din, hidden, dout, params, max_batch=256, stream=None):
+        self.din, self.hidden, self.dout, self.max_batch = int(din), int(hidden), int(dout), int(max_batch)
+        self.np = mlp_num_params(din, hidden, dout)
+        flat = np.ascontiguousarray(params, np.float32).ravel()
+        if flat.size != self.np:
+            raise ValueError("params must hold %d floats" % self.np)
+        ctx = ctypes.c_void_p()
+        _check(lib().gsi_mlp_create(self.din, self.hidden, self.dout, self.max_batch, flat.ctypes.data,
+                                    _stream(stream), ctypes.byref(ctx)), "gsi_mlp_create")
+        self._ctx = ctx
+
+    @staticmethod
+    def flatten(prm):
+        return np.concatenate([np.asarray(prm[k], np.float32).ravel()
+                               for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+    def unflatten(self, flat):
+        d, h, o = self.din, self.hidden, self.dout
+        out, k = {}, 0
+        for name, shape in (("W1", (h, d)), ("b1", (h,)), ("W2", (h, h)), ("b2", (h,)),
+                            ("W3", (o, h)), ("b3", (o,))):
+            size = int(np.prod(shape))
+            out[name] = flat[k:k + size].reshape(shape)
+            k += size
+        return out
+
+    def params(self):
+        w = np.zeros(self.np, np.float32)
+        _check(lib().gsi_mlp_get_params(self._ctx, w.ctypes.data, None), "gsi_mlp_get_params")
+        return self.unflatten(w)
+
+    def grads(self):
+        g = np.zeros(self.np, np.float32)
+        _check(lib().gsi_mlp_get_params(self._ctx, None, g.ctypes.data), "gsi_mlp_get_params")
+        return self.unflatten(g)
+
+    def forward(self, x, out):
+        _check(lib().gsi_mlp_forward(self._ctx, int(x.shape[0]), _f32(x), _f32(out)), "gsi_mlp_forward")
+        return out
+
+    def backward(self, x, dout):
+        _check(lib().gsi_mlp_backward(self._ctx, int(x.shape[0]), _f32(x), _f32(dout)), "gsi_mlp_backward")
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().gsi_mlp_adam(self._ctx, float(lr), float(beta1), float(beta2), float(eps)),
+               "gsi_mlp_adam")
+
+    def train_step(self, x, S, Bt, m, p, lr):
+        """forward, mean-loss gradient, backward, Adam; returns the mean loss.
+        S = (rowptr int64, colidx int32, val float64) CUDA tensors."""
+        import torch
+        loss = ctypes.c_double()
+        _check(lib().gsi_warm_train_step(self._ctx, int(x.shape[0]), _f32(x), int(m), int(p),
+                                         _dptr(S[0], torch.int64), _dptr(S[1], torch.int32),
+                                         _dptr(S[2], torch.float64), _f32(Bt), float(lr), ctypes.byref(loss)),
+               "gsi_warm_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().gsi_mlp_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def warm_loss_grad(C, S, Bt, m, p, gscale=1.0, stream=None):
+    """(loss (batch,), dC) for C, Bt (batch x m x p float32 CUDA tensors)."""
+    import torch
+    batch = int(C.shape[0])
+    loss = torch.empty(batch, dtype=torch.float64, device=C.device)
+    dC = torch.empty_like(C)
+    SC = torch.empty_like(C)
+    _check(lib().gsi_warm_loss_grad(batch, int(m), int(p), _dptr(S[0], torch.int64), _dptr(S[1], torch.int32),
+                                    _dptr(S[2], torch.float64), _f32(C), _f32(Bt), _f32(SC),
+                                    _dptr(loss, torch.float64), _f32(dC), ctypes.c_float(gscale),
+                                    _stream(stream)), "gsi_warm_loss_grad")
+    return loss, dC
+
+
+def prolong(C, nc, nf, p, stream=None):
+    """X (batch x nf^2 x p float64) = P C for C (batch x nc^2 x p float32)."""
+    import torch
+    batch = int(C.shape[0])
+    X = torch.empty((batch, nf * nf, p), dtype=torch.float64, device=C.device)
+    _check(lib().gsi_prolong(int(nc), int(nf), int(p), batch, _f32(C), _dptr(X, torch.float64),
+                             _stream(stream)), "gsi_prolong")
+    return X
+
+
+def restrict(U, nc, nf, p, stream=None):
+    """Bt (batch x nc^2 x p float32) = P^T U for U (batch x nf^2 x p float64)."""
+    import torch
+    batch = int(U.shape[0])
+    Bt = torch.empty((batch, nc * nc, p), dtype=torch.float32, device=U.device)
+    _check(lib().gsi_restrict(int(nc), int(nf), int(p), batch, _dptr(U, torch.float64), _f32(Bt),
+                              _stream(stream)), "gsi_restrict")
+    return Bt
+
+
+def gemm_bf16(M, N, K, A, sa, B, sb, C, ldc, alpha=1.0, beta=0.0, bias=None, mask=None, relu=False,
+              stream=None):
+    """C = alpha op(A) op(B) + beta C (+ bias, mask, ReLU) with strides
+    sa = (sai, sak), sb = (sbk, sbj); float32 CUDA tensors."""
+    _check(lib().gsi_gemm_bf16(int(M), int(N), int(K), _f32(A), int(sa[0]), int(sa[1]), _f32(B), int(sb[0]),
+                               int(sb[1]), _f32(C), int(ldc), ctypes.c_float(alpha), ctypes.c_float(beta),
+                               None if bias is None else _f32(bias), None if mask is None else _f32(mask),
+                               1 if relu else 0, _stream(stream)), "gsi_gemm_bf16")
+    return C
