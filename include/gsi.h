@@ -309,6 +309,15 @@ gsi_status gsi_oz_dense_apply(int64_t n, int32_t p, const float* A, const float*
 gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, const float* V,
                                int32_t sym, double* G, void* stream);
 
+/* Which tensor-core kernels the digit-split products use: 0 (default) the
+ * tcgen05 kernels where they apply (7 digits, p <= 64 for the block
+ * product), 1 the mma.sync kernels everywhere. Both give identical results
+ * (the digit-pair sums are exact integers); the switch exists to compare
+ * them. Process-wide; the environment variable GSI_TENSOR_PATH=mma selects
+ * 1 before the first product. */
+gsi_status gsi_set_tensor_path(int32_t path);
+int32_t gsi_tensor_path(void);
+
 /* ---- batched solver -------------------------------------------------------
  * Many independent problems, each the dominant p_i-dimensional invariant
  * subspace of a symmetric A_i (the problem of Sec. 2.1), iterated together

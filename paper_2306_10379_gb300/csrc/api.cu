@@ -151,4 +151,12 @@ gsi_status gsi_oz_dense_apply(int64_t n, int32_t p, const float* A, const float*
                  reinterpret_cast<float2*>(W));
 }
 
+gsi_status gsi_set_tensor_path(int32_t path) {
+  if (path != 0 && path != 1) return GSI_ERR_ARG;
+  set_tensor_path(path);
+  return GSI_OK;
+}
+
+int32_t gsi_tensor_path(void) { return tensor_path(); }
+
 }  // extern "C"

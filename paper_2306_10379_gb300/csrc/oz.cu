@@ -16,6 +16,8 @@
 // to 256, so the tensor-core accumulation is exact. The 7 group sums are then
 // combined in df64: OUT = 2^(E_r + F_j - 14) sum_g S_g 2^(-7 g).
 #include <cuda_bf16.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "df.cuh"
 #include "oz.cuh"
@@ -23,6 +25,18 @@
 namespace gsi {
 
 constexpr int ND = 7;
+
+// 0: tcgen05 kernels where they apply, 1: mma.sync kernels only (set by
+// gsi_set_tensor_path or GSI_TENSOR_PATH=mma at the first product)
+static int g_tensor_path = -1;
+int tensor_path() {
+  if (g_tensor_path < 0) {
+    const char* e = getenv("GSI_TENSOR_PATH");
+    g_tensor_path = (e && strcmp(e, "mma") == 0) ? 1 : 0;
+  }
+  return g_tensor_path;
+}
+void set_tensor_path(int path) { g_tensor_path = path == 1 ? 1 : 0; }
 constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23: x + MAGIC - MAGIC rounds x to an integer
 
 __device__ __forceinline__ int exponent_above(float maxabs) {
@@ -356,6 +370,295 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// oz_gemm on the 5th-generation tensor cores (tcgen05), for K16 <= 64 and the
+// 7-digit split. 128-row tiles; the 7 digit planes of the tile's left operand
+// and of the right operand live in shared memory in the no-swizzle K-major
+// core-matrix layout (8 x 16-byte cores; K-adjacent cores 128 B apart, 8-row
+// groups K16/8 * 128 B apart). One thread issues the 28 digit-pair products
+// as M = 128, N = NC, K = 16 MMAs into 7 group accumulators in tensor memory
+// (group g at columns g NC); the epilogue reads each row's group sums back
+// (tcgen05.ld, TMEM lane = row) and combines them in df64 as the mma.sync
+// kernel does. The group sums are exact integers either way, so both kernels
+// give identical results.
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 512;
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr int TC_WAIT_LIMIT = 1 << 24;
+
+__device__ int g_oz_tc_timeouts;  // count of bounded waits that ran out
+
+__host__ __device__ inline size_t tc_plane_bytes(int rows, int K16) { return (size_t)rows * K16 * 2; }
+
+size_t oz_gemm_tc_smem(int K16, int NC) {
+  return ND * tc_plane_bytes(TC_M, K16) + ND * tc_plane_bytes(NC, K16) + (TC_M + 64) * sizeof(int) + 64;
+}
+
+__device__ __forceinline__ uint32_t tc_off(int r, int k, int K16) {
+  return (uint32_t)((((r >> 3) * (K16 >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// shared-memory matrix descriptor: start, leading (K) core stride 128 B,
+// stride (8-row group) K16/8 * 128 B, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, int K16) {
+  const uint64_t sbo = (uint64_t)((K16 >> 3) * 128);
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | (((sbo >> 4) & 0x3FFFu) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+        "selp.b32 %0, 1, 0, P1;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void tc_ld8(uint32_t r[8], uint32_t taddr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_ld4(uint32_t r[4], uint32_t taddr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
+  extern __shared__ __align__(16) unsigned char tc_smem[];
+  unsigned char* smem = tc_smem;
+  const int col0 = blockIdx.y * 64;
+  const int NC = min(64, p16 - col0);
+  const uint32_t aplane = (uint32_t)tc_plane_bytes(TC_M, K16), bplane = (uint32_t)tc_plane_bytes(NC, K16);
+  unsigned char* Ad = smem;
+  unsigned char* Bd = Ad + ND * aplane;
+  int* Er = reinterpret_cast<int*>(Bd + ND * bplane);
+  int* Fs = Er + TC_M;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Fs + 64);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool two = a.fuse_u1 != 0;
+
+  // right operand digits (Md[plane][n][k]) into the core-matrix layout
+  for (int e = tid; e < ND * NC * (K16 / 8); e += TC_THREADS) {
+    const int c = e % (K16 / 8), rowi = e / (K16 / 8), plane = rowi / NC, nn = rowi - plane * NC;
+    const uint4 v = *reinterpret_cast<const uint4*>(a.Md + ((size_t)plane * p16 + col0 + nn) * K16 + c * 8);
+    *reinterpret_cast<uint4*>(Bd + plane * bplane + tc_off(nn, c * 8, K16)) = v;
+  }
+  for (int e = tid; e < NC; e += TC_THREADS) Fs[e] = a.F[col0 + e];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NC >> 3) << 17) |
+                         ((uint32_t)(TC_M >> 4) << 24);
+  const uint32_t abase = smem_addr(Ad), bbase = smem_addr(Bd), mb = smem_addr(mbar);
+  float2 dacc0 = make_float2(0.f, 0.f), dacc1 = make_float2(0.f, 0.f);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int64_t ntiles = (n + TC_M - 1) / TC_M;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * TC_M;
+    // (a) the tile's left operand, 8 rows per warp at a time: lane = (row
+    // rr = lane / 4, pair j = lane % 4) holds columns 8c + 2j, 8c + 2j + 1;
+    // global reads are 64-byte row segments and the digit stores hit 32
+    // different banks (row stride 16 B, pair stride 4 B in a core matrix)
+    for (int rb = warp * 8; rb < TC_M; rb += (TC_THREADS / 32) * 8) {
+      const int rr = rb + (lane >> 2), j = lane & 3;
+      const int64_t R = r0 + rr;
+      const bool live = R < n;
+      float2 xr[16];
+      float mx = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int k = 8 * c + 2 * j;
+        float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
+        if (live && k < p) {
+          const int64_t o = R * p + k;
+          if (k + 1 < p && (o & 1) == 0) {  // 16-byte aligned pair
+            const float4 v = *reinterpret_cast<const float4*>(a.U[0] + o);
+            x0 = make_float2(v.x, v.y);
+            x1 = make_float2(v.z, v.w);
+            if (two) {
+              const float4 u = *reinterpret_cast<const float4*>(a.U[1] + o);
+              x0 = df_add(x0, df_mul(a.a1, make_float2(u.x, u.y)));
+              x1 = df_add(x1, df_mul(a.a1, make_float2(u.z, u.w)));
+            }
+          } else {
+            x0 = a.U[0][o];
+            if (two) x0 = df_add(x0, df_mul(a.a1, a.U[1][o]));
+            if (k + 1 < p) {
+              x1 = a.U[0][o + 1];
+              if (two) x1 = df_add(x1, df_mul(a.a1, a.U[1][o + 1]));
+            }
+          }
+        }
+        xr[2 * c] = x0;
+        xr[2 * c + 1] = x1;
+        mx = fmaxf(mx, fmaxf(fabsf(x0.x), fabsf(x1.x)));
+      }
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      const int E = exponent_above(mx);
+      if (j == 0) Er[rr] = E;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (8 * c < K16) {
+          float d0[ND], d1[ND];
+          digitsN<ND>(xr[2 * c].x, xr[2 * c].y, E, d0);
+          digitsN<ND>(xr[2 * c + 1].x, xr[2 * c + 1].y, E, d1);
+#pragma unroll
+          for (int i = 0; i < ND; ++i)
+            *reinterpret_cast<uint32_t*>(Ad + i * aplane + tc_off(rr, 8 * c + 2 * j, K16)) =
+                pack_bf16x2(d0[i], d1[i]);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // (b) the 28 digit-pair products, grouped by g = i + j
+    if (tid == 0) {
+      for (int g = 0; g < ND; ++g)
+        for (int i = 0; i <= g; ++i)
+          for (int ks = 0; ks < K16 / 16; ++ks)
+            tc_mma(tmem + (uint32_t)(g * NC), tc_desc(abase + i * aplane + ks * 256, K16),
+                   tc_desc(bbase + (g - i) * bplane + ks * 256, K16), idesc, (i > 0 || ks > 0) ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                   : "memory");
+    }
+    const bool done = tc_wait(mb, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!done)) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // (c) epilogue, part 1: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its
+    // rows) and the column quarter w / 4, 4 columns at a time; the combined
+    // and scaled products go to shared memory (the digit planes are free once
+    // the products completed: 128 (NC + 1) float2 <= 7 * 128 * K16 bf16 for
+    // NC = K16 >= 16), row stride NC + 1 float2 (two wavefronts per warp store)
+    float2* stage = reinterpret_cast<float2*>(Ad);
+    const int ss = NC + 1;
+    {
+      const int row = 32 * (warp & 3) + lane;
+      const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+      const int quarter = NC / 4, cbeg = (warp >> 2) * quarter;
+      for (int c0 = cbeg; c0 < cbeg + quarter; c0 += 4) {
+        uint32_t v[ND][4];
+#pragma unroll
+        for (int g = 0; g < ND; ++g) tc_ld4(v[g], lanes + (uint32_t)(g * NC + c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e2 = 0; e2 < 4; ++e2) {
+          float S[ND];
+#pragma unroll
+          for (int g = 0; g < ND; ++g) S[g] = __uint_as_float(v[g][e2]);
+          const float2 w = combine_groups<ND>(S);
+          const int sc = Er[row] + Fs[c0 + e2] - 14;
+          float2 y;
+          if (sc >= -126) {
+            const float f = exp2i(sc);
+            y = make_float2(w.x * f, w.y * f);
+          } else {
+            const float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
+            y = make_float2(w.x * f1 * f2, w.y * f1 * f2);
+          }
+          stage[row * ss + c0 + e2] = y;
+        }
+      }
+    }
+    __syncthreads();
+    // part 2: row-contiguous pass over the tile: elementwise terms, dots and
+    // the store, coalesced
+    for (int e = tid; e < TC_M * NC; e += TC_THREADS) {
+      const int rr = e / NC, cc = e - rr * NC;
+      const int64_t R = r0 + rr;
+      const int C = col0 + cc;
+      if (R >= n || C >= p) continue;
+      float2 y = stage[rr * ss + cc];
+      const int64_t idx = R * p + C;
+      for (int m = 0; m < a.ne; ++m) y = df_add(y, df_mul(a.ce[m], a.E[m][idx]));
+      if (a.dot_self) dacc0 = df_add(dacc0, df_mul(y, y));
+      if (a.dot_with) dacc1 = df_add(dacc1, df_mul(y, a.dot_with[idx]));
+      a.out[idx] = y;
+    }
+    // the next tile rewrites Er and the digit planes: every warp leaves the
+    // epilogue first
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (failed) {
+    // a product that did not complete: count it, wait once more for the
+    // tensor core (bounded), poison this block's rows so the caller sees
+    // non-finite values, and release the tensor memory
+    if (tid == 0) atomicAdd(&g_oz_tc_timeouts, 1);
+    tc_wait(mb, phase ^ 1u);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+      for (int e = tid; e < TC_M * NC; e += TC_THREADS) {
+        const int64_t R = tile * TC_M + e / NC;
+        const int c = e % NC;
+        if (R < n && col0 + c < p) a.out[R * p + col0 + c] = make_float2(NAN, NAN);
+      }
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  if (a.dot_part) {
+    __shared__ float2 red[2][TC_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+      float2 t0 = make_float2(__shfl_xor_sync(0xffffffffu, dacc0.x, o), __shfl_xor_sync(0xffffffffu, dacc0.y, o));
+      float2 t1 = make_float2(__shfl_xor_sync(0xffffffffu, dacc1.x, o), __shfl_xor_sync(0xffffffffu, dacc1.y, o));
+      dacc0 = df_add(dacc0, t0);
+      dacc1 = df_add(dacc1, t1);
+    }
+    if ((tid & 31) == 0) {
+      red[0][warp] = dacc0;
+      red[1][warp] = dacc1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+      for (int w = 0; w < TC_THREADS / 32; ++w) {
+        s0 = df_add(s0, red[0][w]);
+        s1 = df_add(s1, red[1][w]);
+      }
+      const int b = blockIdx.y * gridDim.x + blockIdx.x;
+      a.dot_part[2 * b] = s0;
+      a.dot_part[2 * b + 1] = s1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // oz_gram: G = U^T V. Output in 64 x 64 blocks (blockIdx.y), rows in chunks of
 // GR_KC = 64 processed by the blocks of blockIdx.x in turn. 16 warps, each a
 // 16 x 16 output tile (2 n-tiles); per chunk the column exponents are taken
@@ -617,6 +920,16 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   a.dot_with = dot_with;
   a.dot_self = dot_self ? 1 : 0;
   const int NCmax = std::min(64, p16);
+  if (nd == ND && K16 <= 64 && tensor_path() == 0) {
+    const size_t tsm = oz_gemm_tc_smem(K16, NCmax);
+    GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    int gx = (int)std::min<int64_t>((n + TC_M - 1) / TC_M, (int64_t)sm_count());
+    gx = std::max(gx, 1);
+    if (nparts) *nparts = gx * ncs;
+    oz_gemm_tc_kernel<<<dim3(gx, ncs), TC_THREADS, tsm, st>>>(n, p, p16, K16, a);
+    GSI_LAUNCH_CHECK();
+    return GSI_OK;
+  }
   size_t smem = oz_gemm_smem(K16, NCmax, fuse ? 2 : 1, nd);
   auto kern = nd == 3 ? oz_gemm_kernel<3> : oz_gemm_kernel<ND>;
   GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

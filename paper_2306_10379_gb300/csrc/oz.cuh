@@ -23,6 +23,9 @@ struct OzGemmArgs {
 };
 
 int pad16(int x);
+// 0: tcgen05 kernels where they apply; 1: mma.sync kernels only
+int tensor_path();
+void set_tensor_path(int path);
 size_t oz_rhs_bytes(int p, int nk);
 // OUT = sum_{k<nk} U_k (s_k M_k) + sum_{e<ne} ce_e E_e; M_k float64 p x p (device).
 // With nk = 2 and M_1 == M_0 the left operand U_0 + (s_1/s_0) U_1 is formed in

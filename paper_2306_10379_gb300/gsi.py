@@ -143,6 +143,10 @@ def _lib():
         L.gsi_last_error.restype = ctypes.c_char_p
         L.gsi_launch_count.argtypes = []
         L.gsi_launch_count.restype = ctypes.c_int64
+        L.gsi_set_tensor_path.argtypes = [i32]
+        L.gsi_set_tensor_path.restype = ctypes.c_int
+        L.gsi_tensor_path.argtypes = []
+        L.gsi_tensor_path.restype = ctypes.c_int32
         L.gsi_mlp_num_params.argtypes = [i32, i32, i32]
         L.gsi_mlp_num_params.restype = ctypes.c_int64
         _LIB = L
@@ -260,6 +264,15 @@ def retract(t, M, X, D, Y, W, stream=None):
     f = torch.float64
     _check(lib().gsi_retract(n, p, float(t), _dptr(M, f, (p, p)), _dptr(X, f), _dptr(D, f, (n, p)),
                              _dptr(Y, f, (n, p)), _dptr(W, f, (n, p)), _stream(stream)), "gsi_retract")
+
+
+def set_tensor_path(path):
+    """0: tcgen05 kernels where they apply (default); 1: mma.sync kernels only."""
+    _check(lib().gsi_set_tensor_path(int(path)), "gsi_set_tensor_path")
+
+
+def tensor_path():
+    return int(lib().gsi_tensor_path())
 
 
 def launch_count():

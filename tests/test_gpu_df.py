@@ -146,3 +146,27 @@ def test_oz_gemm_fused_left_sum(G, n, p):
     got = gsi.from_df(out.cpu().numpy())
     bound = (np.abs(U0) + t * np.abs(U1)).max(1, keepdims=True) * np.abs(M).max(0, keepdims=True) * p * 2.0 ** -44
     assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("n,p,fused,ne", [(4099, 64, True, 2), (1000, 16, False, 1), (257, 48, True, 0),
+                                          (130, 8, False, 2), (70001, 64, True, 1)])
+def test_oz_gemm_tcgen05_equals_mma(G, n, p, fused, ne):
+    """The tcgen05 block product (tensor memory accumulators) and the mma.sync
+    one sum the same exact integer digit products and combine them in the
+    same order: bit-identical results, including the fused left sum
+    (X + tD) M and the elementwise terms."""
+    torch, gsi = G
+    rng = np.random.default_rng(n + 3 * p)
+    U0 = _df_dev(torch, gsi, _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-3, 3, (n, 1)))))
+    U1 = _df_dev(torch, gsi, _exact(gsi, rng.standard_normal((n, p)))) if fused else None
+    M = torch.from_numpy(rng.standard_normal((p, p)) * np.exp(rng.uniform(-2, 2, (1, p)))).cuda()
+    E = [_df_dev(torch, gsi, _exact(gsi, rng.standard_normal((n, p)))) for _ in range(ne)]
+    outs = []
+    for path in (0, 1):
+        gsi.set_tensor_path(path)
+        out = torch.zeros((n, p, 2), dtype=torch.float32, device="cuda")
+        gsi.oz_gemm(U0, M, out, s0=0.7, U1=U1, M1=M if fused else None, s1=0.3 if fused else 0.0,
+                    E=E, c=[0.3, -2.5][:ne])
+        outs.append(out.cpu().numpy())
+    gsi.set_tensor_path(0)
+    assert np.array_equal(outs[0], outs[1])
