@@ -152,7 +152,7 @@ gsi_status gsi_oz_dense_apply(int64_t n, int32_t p, const float* A, const float*
 }
 
 gsi_status gsi_set_tensor_path(int32_t path) {
-  if (path != 0 && path != 1) return GSI_ERR_ARG;
+  if (path < 0 || path > 2) return GSI_ERR_ARG;
   set_tensor_path(path);
   return GSI_OK;
 }

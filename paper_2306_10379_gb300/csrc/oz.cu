@@ -26,17 +26,19 @@ namespace gsi {
 
 constexpr int ND = 7;
 
-// 0: tcgen05 kernels where they apply, 1: mma.sync kernels only (set by
-// gsi_set_tensor_path or GSI_TENSOR_PATH=mma at the first product)
+// 0: tcgen05 kernels where they are the faster ones (block products and
+// symmetric Grams with p <= 64), 1: mma.sync kernels only, 2: tcgen05
+// kernels wherever they apply (set by gsi_set_tensor_path, or by
+// GSI_TENSOR_PATH=mma / =tcgen05 at the first product)
 static int g_tensor_path = -1;
 int tensor_path() {
   if (g_tensor_path < 0) {
     const char* e = getenv("GSI_TENSOR_PATH");
-    g_tensor_path = (e && strcmp(e, "mma") == 0) ? 1 : 0;
+    g_tensor_path = (e && strcmp(e, "mma") == 0) ? 1 : (e && strcmp(e, "tcgen05") == 0) ? 2 : 0;
   }
   return g_tensor_path;
 }
-void set_tensor_path(int path) { g_tensor_path = path == 1 ? 1 : 0; }
+void set_tensor_path(int path) { g_tensor_path = (path == 1 || path == 2) ? path : 0; }
 constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23: x + MAGIC - MAGIC rounds x to an integer
 
 __device__ __forceinline__ int exponent_above(float maxabs) {
@@ -484,46 +486,54 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   uint32_t phase = 0;
   bool failed = false;
   const int64_t ntiles = (n + TC_M - 1) / TC_M;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t r0 = tile * TC_M;
-    // (a) the tile's left operand, 8 rows per warp at a time: lane = (row
-    // rr = lane / 4, pair j = lane % 4) holds columns 8c + 2j, 8c + 2j + 1;
-    // global reads are 64-byte row segments and the digit stores hit 32
-    // different banks (row stride 16 B, pair stride 4 B in a core matrix)
-    for (int rb = warp * 8; rb < TC_M; rb += (TC_THREADS / 32) * 8) {
-      const int rr = rb + (lane >> 2), j = lane & 3;
-      const int64_t R = r0 + rr;
-      const bool live = R < n;
-      float2 xr[16];
-      float mx = 0.0f;
+  // lane = (row rr = rb + lane / 4 of the warp's 8 rows, pair j = lane % 4)
+  // holds columns 8c + 2j, 8c + 2j + 1 (c < 8); one round of 8 rows per warp
+  // (16 warps, 128-row tiles). The next tile's rows are loaded (and the fused
+  // left sum formed) while the current tile's products run.
+  static_assert(TC_THREADS / 32 * 8 == TC_M, "one 8-row round per warp");
+  const int rb = warp * 8, rr = rb + (lane >> 2), j = lane & 3;
+  float2 xr[16];
+  auto load_tile = [&](int64_t t) {
+    const int64_t R = t * TC_M + rr;
+    const bool live = t < ntiles && R < n;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int k = 8 * c + 2 * j;
-        float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
-        if (live && k < p) {
-          const int64_t o = R * p + k;
-          if (k + 1 < p && (o & 1) == 0) {  // 16-byte aligned pair
-            const float4 v = *reinterpret_cast<const float4*>(a.U[0] + o);
-            x0 = make_float2(v.x, v.y);
-            x1 = make_float2(v.z, v.w);
-            if (two) {
-              const float4 u = *reinterpret_cast<const float4*>(a.U[1] + o);
-              x0 = df_add(x0, df_mul(a.a1, make_float2(u.x, u.y)));
-              x1 = df_add(x1, df_mul(a.a1, make_float2(u.z, u.w)));
-            }
-          } else {
-            x0 = a.U[0][o];
-            if (two) x0 = df_add(x0, df_mul(a.a1, a.U[1][o]));
-            if (k + 1 < p) {
-              x1 = a.U[0][o + 1];
-              if (two) x1 = df_add(x1, df_mul(a.a1, a.U[1][o + 1]));
-            }
+    for (int c = 0; c < 8; ++c) {
+      const int k = 8 * c + 2 * j;
+      float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
+      if (live && k < p) {
+        const int64_t o = R * p + k;
+        if (k + 1 < p && (o & 1) == 0) {  // 16-byte aligned pair
+          const float4 v = *reinterpret_cast<const float4*>(a.U[0] + o);
+          x0 = make_float2(v.x, v.y);
+          x1 = make_float2(v.z, v.w);
+          if (two) {
+            const float4 u = *reinterpret_cast<const float4*>(a.U[1] + o);
+            x0 = df_add(x0, df_mul(a.a1, make_float2(u.x, u.y)));
+            x1 = df_add(x1, df_mul(a.a1, make_float2(u.z, u.w)));
+          }
+        } else {
+          x0 = a.U[0][o];
+          if (two) x0 = df_add(x0, df_mul(a.a1, a.U[1][o]));
+          if (k + 1 < p) {
+            x1 = a.U[0][o + 1];
+            if (two) x1 = df_add(x1, df_mul(a.a1, a.U[1][o + 1]));
           }
         }
-        xr[2 * c] = x0;
-        xr[2 * c + 1] = x1;
-        mx = fmaxf(mx, fmaxf(fabsf(x0.x), fabsf(x1.x)));
       }
+      xr[2 * c] = x0;
+      xr[2 * c + 1] = x1;
+    }
+  };
+  load_tile(blockIdx.x);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * TC_M;
+    // (a) the tile's left operand: row maxima and digits; global reads were
+    // 64-byte row segments, and the digit stores hit 32 different banks (row
+    // stride 16 B, pair stride 4 B in a core matrix)
+    {
+      float mx = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) mx = fmaxf(mx, fabsf(xr[c].x));
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
       const int E = exponent_above(mx);
@@ -555,6 +565,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
                    : "memory");
     }
+    load_tile(tile + gridDim.x);  // registers only: the digit planes are in use
     const bool done = tc_wait(mb, phase);
     phase ^= 1u;
     if (__syncthreads_or(!done)) {
@@ -828,6 +839,186 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
   }
 }
 
+// ---------------------------------------------------------------------------
+// oz_gram on the 5th-generation tensor cores, for p, q <= 64 and the 7-digit
+// split: the same 64-row chunks, per-chunk column exponents, digits and df64
+// accumulation as oz_gram_kernel (identical partial sums), with the 28
+// digit-pair products issued by one thread as M = 64, N = 64, K = 16 tcgen05
+// MMAs into 7 tensor-memory group accumulators. Output row i of an M = 64
+// product sits in TMEM lane 32 (i / 16) + i % 16. With U == V (sym) the
+// digits are cut once.
+// ---------------------------------------------------------------------------
+constexpr int TG_KC = 64;
+constexpr int TG_THREADS = 512;
+
+size_t oz_gram_tc_smem() {
+  return (size_t)2 * ND * 64 * TG_KC * 2 + 8 * 128 * sizeof(float) + 128 * sizeof(int) + 64;
+}
+
+__global__ void __launch_bounds__(TG_THREADS, 1)
+oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
+                  int sym, float2* part) {
+  extern __shared__ __align__(16) unsigned char tg_smem[];
+  const uint32_t plane = 64 * TG_KC * 2;
+  unsigned char* Ad = tg_smem;
+  unsigned char* Bd = Ad + ND * plane;
+  float* cmx = reinterpret_cast<float*>(Bd + ND * plane);  // [8][128] partial column maxima
+  int* Eu = reinterpret_cast<int*>(cmx + 8 * 128);
+  int* Ev = Eu + 64;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Ev + 64);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
+  const uint32_t abase = smem_addr(Ad), bbase = smem_addr(sym ? Ad : Bd), mb = smem_addr(mbar);
+  const int* Evv = sym ? Eu : Ev;
+  // this thread's outputs: row i = 16 (warp % 4) + lane (lanes < 16), columns
+  // 16 (warp / 4) + 0..15
+  float2 res[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) res[e] = make_float2(0.f, 0.f);
+  const int orow = 16 * (warp & 3) + (lane & 15), cbase = 16 * (warp >> 2);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int64_t nchunks = (n + TG_KC - 1) / TG_KC;
+  // thread <-> column c and the chunk rows 2 rp + h + 16 k (k < 4, h < 2);
+  // the next chunk's values are loaded while the current products run
+  const int c = tid & 63, rp = tid >> 6;
+  float2 xu[8], xv[8];
+  auto load_chunk = [&](int64_t chunk) {
+    const int64_t rb = chunk * TG_KC;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t R = rb + 16 * k + 2 * rp + h;
+        const bool ok = chunk < nchunks && R < n;
+        xu[2 * k + h] = (ok && c < p) ? U[R * p + c] : make_float2(0.f, 0.f);
+        if (!sym) xv[2 * k + h] = (ok && c < q) ? V[R * q + c] : make_float2(0.f, 0.f);
+      }
+  };
+  load_chunk(blockIdx.x);
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    // (a) the chunk's column maxima of |hi|
+    float mu = 0.f, mv = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      mu = fmaxf(mu, fabsf(xu[k].x));
+      if (!sym) mv = fmaxf(mv, fabsf(xv[k].x));
+    }
+    cmx[rp * 128 + c] = mu;
+    cmx[rp * 128 + 64 + c] = mv;
+    __syncthreads();
+    if (tid < 128) {
+      float m = 0.f;
+      for (int g = 0; g < 8; ++g) m = fmaxf(m, cmx[g * 128 + tid]);
+      if (tid < 64) Eu[tid] = exponent_above(m);
+      else Ev[tid - 64] = exponent_above(m);
+    }
+    __syncthreads();
+    // (b) digits into the K-major planes: element (row r, column c) of the
+    // chunk is entry (m = c, k = r); pairs of rows pack into one word
+    {
+      const int Ec = Eu[c];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = 16 * k + 2 * rp;
+        float d0[ND], d1[ND];
+        digitsN<ND>(xu[2 * k].x, xu[2 * k].y, Ec, d0);
+        digitsN<ND>(xu[2 * k + 1].x, xu[2 * k + 1].y, Ec, d1);
+#pragma unroll
+        for (int i = 0; i < ND; ++i)
+          *reinterpret_cast<uint32_t*>(Ad + i * plane + tc_off(c, r, TG_KC)) = pack_bf16x2(d0[i], d1[i]);
+      }
+      if (!sym) {
+        const int Fc = Ev[c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int r = 16 * k + 2 * rp;
+          float d0[ND], d1[ND];
+          digitsN<ND>(xv[2 * k].x, xv[2 * k].y, Fc, d0);
+          digitsN<ND>(xv[2 * k + 1].x, xv[2 * k + 1].y, Fc, d1);
+#pragma unroll
+          for (int i = 0; i < ND; ++i)
+            *reinterpret_cast<uint32_t*>(Bd + i * plane + tc_off(c, r, TG_KC)) = pack_bf16x2(d0[i], d1[i]);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // (c) the 28 digit-pair products, grouped by g = i + j
+    if (tid == 0) {
+      for (int g = 0; g < ND; ++g)
+        for (int i = 0; i <= g; ++i)
+          for (int ks = 0; ks < TG_KC / 16; ++ks)
+            tc_mma(tmem + (uint32_t)(g * 64), tc_desc(abase + i * plane + ks * 256, TG_KC),
+                   tc_desc(bbase + (g - i) * plane + ks * 256, TG_KC), idesc, (i > 0 || ks > 0) ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                   : "memory");
+    }
+    load_chunk(ch + gridDim.x);  // registers only: the digit planes are in use
+    const bool done = tc_wait(mb, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!done)) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // (d) group sums back from tensor memory, combined and scaled per chunk
+    {
+      const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll
+      for (int c0 = 0; c0 < 16; c0 += 4) {
+        uint32_t v[ND][4];
+#pragma unroll
+        for (int g = 0; g < ND; ++g) tc_ld4(v[g], lanes + (uint32_t)(g * 64 + cbase + c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (lane < 16) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float S[ND];
+#pragma unroll
+            for (int g = 0; g < ND; ++g) S[g] = __uint_as_float(v[g][e]);
+            const float2 w = combine_groups<ND>(S);
+            const int sc = Eu[orow] + Evv[cbase + c0 + e] - 14;
+            const float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
+            res[c0 + e] = df_add(res[c0 + e], make_float2(w.x * f1 * f2, w.y * f1 * f2));
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (failed) {
+    if (tid == 0) atomicAdd(&g_oz_tc_timeouts, 1);
+    tc_wait(mb, phase ^ 1u);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) res[e] = make_float2(NAN, NAN);
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  if (lane < 16) {
+    float2* out = part + (size_t)blockIdx.x * 4096;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) out[orow * 64 + cbase + e] = res[e];
+  }
+}
+
 // Fixed-order sum of the per-block partials into G (float64, p x q); the
 // symmetric case fills the lower triangle from the upper one.
 __global__ void oz_gram_reduce_kernel(int p, int q, int nsplit, int nblk, int sym, int nbj,
@@ -920,7 +1111,7 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   a.dot_with = dot_with;
   a.dot_self = dot_self ? 1 : 0;
   const int NCmax = std::min(64, p16);
-  if (nd == ND && K16 <= 64 && tensor_path() == 0) {
+  if (nd == ND && K16 <= 64 && tensor_path() != 1) {
     const size_t tsm = oz_gemm_tc_smem(K16, NCmax);
     GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
     int gx = (int)std::min<int64_t>((n + TC_M - 1) / TC_M, (int64_t)sm_count());
@@ -988,12 +1179,21 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
   const int nbj = (q + 63) / 64;
   const int nblk = oz_gram_blocks(p, q, sym);
   const int ns = oz_gram_splits(n, p, q, sym);
-  size_t smem = oz_gram_smem(nd);
-  auto kern = nd == 3 ? oz_gram_kernel<3> : oz_gram_kernel<ND>;
-  GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  GSI_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)ns * nblk * 4096 * sizeof(float2), st));
-  kern<<<dim3(ns, nblk), GR_THREADS, smem, st>>>(n, p, q, U, V, sym ? 1 : 0, nbj, scratch);
-  GSI_LAUNCH_CHECK();
+  const int tp = tensor_path();
+  if (nd == ND && p <= 64 && q <= 64 && (tp == 2 || (tp == 0 && sym))) {
+    // one 64 x 64 output block; every partial entry is written
+    const size_t tsm = oz_gram_tc_smem();
+    GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    oz_gram_tc_kernel<<<ns, TG_THREADS, tsm, st>>>(n, p, q, U, V, sym ? 1 : 0, scratch);
+    GSI_LAUNCH_CHECK();
+  } else {
+    size_t smem = oz_gram_smem(nd);
+    auto kern = nd == 3 ? oz_gram_kernel<3> : oz_gram_kernel<ND>;
+    GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GSI_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)ns * nblk * 4096 * sizeof(float2), st));
+    kern<<<dim3(ns, nblk), GR_THREADS, smem, st>>>(n, p, q, U, V, sym ? 1 : 0, nbj, scratch);
+    GSI_LAUNCH_CHECK();
+  }
   if (Gdf) {
     oz_gram_reduce_df_kernel<<<ceil_div((int64_t)p * q, 256), 256, 0, st>>>(p, q, ns, nbj, scratch, Gdf);
   } else {

@@ -267,7 +267,7 @@ def retract(t, M, X, D, Y, W, stream=None):
 
 
 def set_tensor_path(path):
-    """0: tcgen05 kernels where they apply (default); 1: mma.sync kernels only."""
+    """0: tcgen05 kernels where faster (default); 1: mma.sync only; 2: tcgen05 wherever they apply."""
     _check(lib().gsi_set_tensor_path(int(path)), "gsi_set_tensor_path")
 
 

@@ -162,11 +162,31 @@ def test_oz_gemm_tcgen05_equals_mma(G, n, p, fused, ne):
     M = torch.from_numpy(rng.standard_normal((p, p)) * np.exp(rng.uniform(-2, 2, (1, p)))).cuda()
     E = [_df_dev(torch, gsi, _exact(gsi, rng.standard_normal((n, p)))) for _ in range(ne)]
     outs = []
-    for path in (0, 1):
+    for path in (2, 1):
         gsi.set_tensor_path(path)
         out = torch.zeros((n, p, 2), dtype=torch.float32, device="cuda")
         gsi.oz_gemm(U0, M, out, s0=0.7, U1=U1, M1=M if fused else None, s1=0.3 if fused else 0.0,
                     E=E, c=[0.3, -2.5][:ne])
         outs.append(out.cpu().numpy())
+    gsi.set_tensor_path(0)
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("n,p,q,sym", [(100003, 64, 64, True), (100003, 64, 64, False), (4097, 17, 40, False),
+                                       (70, 8, 8, True), (200000, 48, 5, False)])
+def test_oz_gram_tcgen05_equals_mma(G, n, p, q, sym):
+    """The tcgen05 Gram (tensor-memory group accumulators) and the mma.sync one
+    cut the same chunks into the same digits, sum the same exact integer
+    products and accumulate them in the same order: bit-identical Grams."""
+    torch, gsi = G
+    rng = np.random.default_rng(n + p + q)
+    U = _df_dev(torch, gsi, _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-3, 3, (n, 1)))))
+    V = U if sym else _df_dev(torch, gsi, _exact(gsi, rng.standard_normal((n, q))))
+    outs = []
+    for path in (2, 1):
+        gsi.set_tensor_path(path)
+        Gm = torch.zeros((p, q), dtype=torch.float64, device="cuda")
+        gsi.oz_gram(U, V, Gm, sym=sym)
+        outs.append(Gm.cpu().numpy())
     gsi.set_tensor_path(0)
     assert np.array_equal(outs[0], outs[1])
