@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="fd3d", choices=["fd3d", "dense", "batched", "warm"],
+                    help="fd3d (default): the 128^3 plain solve; dense: mixed precision against "
+                         "float64 on a dense n = 16384, p = 128 spectrum; batched: 512 Erdos-Renyi "
+                         "problems in one graph launch against the plain solver one problem at a "
+                         "time; warm: learned against random start on a diffusion family")
     return ap.parse_args()
 
 
@@ -189,10 +194,229 @@ def run_reference(args):
     return 0
 
 
+
+# ---------------------------------------------------------------------------
+# Further workloads (not the default line): the precision, batching and
+# warm-start forms against the plain float64-class GPU solve of the same
+# problems. Each prints one JSON line with the comparison in "baseline".
+# ---------------------------------------------------------------------------
+
+def _line(args, metric, value, cfg, dtype, extra):
+    out = {"metric": metric, "value": value, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def _timed(torch, fn, steps):
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = [fn() for _ in range(steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, res[-1]
+
+
+def run_dense(args):
+    """Dense A = Q diag(lam) Q^T (n = 16384, p = 128, gap 1e-2 above the rest of
+    the spectrum): the mixed-precision solve (3-digit direction apply, 7-digit
+    correction phase) against the float64 and df64 solves of the same problem."""
+    import numpy as np
+    import torch
+    from paper_2306_10379_gb300 import build, gsi, inputs as I
+    build.build()
+    n, p = 16384, 128
+    A, lam = I.dense_spectrum(n, p, 1e-2, I.SEED_BASE + 3)
+    X0 = torch.from_numpy(I.start_block(n, p, I.SEED_BASE + 3)).cuda()
+    Ad = gsi.Dense(torch.from_numpy(A).cuda())
+    res = {}
+    for prec in ("mixed", "df64", "f64"):
+        s = gsi.Solver(Ad, p, X0, method="cg", tol=1e-8, anorm=float(lam[0]), precision=prec)
+        reps = args.steps if prec == "mixed" else 1
+        if prec == "mixed":
+            for _ in range(args.warmup):
+                s.reset(X0)
+                s.step(20)
+            clocks = ClockSampler(0)
+            clocks.start()
+            l0 = gsi.launch_count()
+        ms, info = _timed(torch, lambda: (s.reset(X0), s.solve())[1], reps)
+        if prec == "mixed":
+            clk = clocks.stop()
+            launches = gsi.launch_count() - l0
+        _, ev = s.basis()
+        res[prec] = {"ms": ms, "iters": info["iters"], "rel_residual": info["rel_residual"],
+                     "ritz_max_abs_err": float(np.max(np.abs(ev - lam[:p])))}
+        s.close()
+    m = res["mixed"]
+    _line(args, "ms to rel. residual 1e-8 (mixed precision vs float64 GPU)", m["ms"],
+          {"workload": "dense A = Q diag(lam) Q^T, n=16384, p=128 largest, gap 1e-2, RCG, rel. residual 1e-8",
+           "n": n, "p": p, "precision": "mixed (3-digit apply, 7-digit correction)", "iterations": m["iters"],
+           "rel_residual": m["rel_residual"], "ritz_max_abs_err": m["ritz_max_abs_err"]},
+          "bf16 tensor-core digits (3 then 7 per operand), df64 blocks, f64 p x p",
+          {"baseline": {"plain_f64_gpu": res["f64"], "df64_gpu": res["df64"],
+                        "speedup_vs_f64": res["f64"]["ms"] / m["ms"]},
+           "clocks": clk, "gpu_launches": launches})
+
+
+def run_batched(args):
+    """512 Erdos-Renyi graph Laplacians (mean degree 8, diagonal shift U(0,1),
+    n_i ~ U[2048, 65536], p_i ~ U{4, 8, 16, 32}), dominant p_i-dimensional
+    subspaces by CG to 1e-8 in one while-graph launch, against the plain
+    solver run one problem after another on a sample of the same problems."""
+    import numpy as np
+    import torch
+    from paper_2306_10379_gb300 import build, gsi, inputs as I
+    build.build()
+    t0 = time.time()
+    B = I.er_batch(512, I.SEED_BASE + 4)
+    gen_s = time.time() - t0
+    b = gsi.Batch(B, method="cg", tol=1e-8, max_iters=5000)
+    tuned = b.tune(3)
+    for _ in range(args.warmup):  # warm-up: the same passes, capped
+        b.reset()
+        b.step(30)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = gsi.launch_count()
+    times = []
+    for _ in range(args.steps):
+        b.reset()
+        ms, passes = _timed(torch, lambda: b.solve(use_graph=True, check=False), 1)
+        times.append(ms)
+    clk = clocks.stop()
+    launches = gsi.launch_count() - l0
+    infos = [b.info(i) for i in range(B.nprob)]
+    b.close()
+    its = np.array([f["iters"] for f in infos])
+    conv = int(sum(f["converged"] for f in infos))
+    # the plain solver, one problem at a time, on the first 6 problems
+    sample = 6
+    plain_ms = 0.0
+    plain_its = []
+    for i in range(sample):
+        m = B.mats[i]
+        s = gsi.Solver(m, int(B.p[i]), B.X0s[i], method="cg", tol=1e-8, max_iters=5000)
+        ms, info = _timed(torch, lambda: s.solve(), 1)
+        s.close()
+        plain_ms += ms
+        plain_its.append(info["iters"])
+    est = plain_ms / sample * B.nprob
+    value = float(np.mean(times))
+    _line(args, "ms to rel. residual 1e-8 (batched vs one-at-a-time GPU)", value,
+          {"workload": "512 Erdos-Renyi graph Laplacians + diag U(0,1), n_i in [2048, 65536], "
+                       "p_i in {4,8,16,32}, RCG, rel. residual 1e-8, one while-graph launch",
+           "problems": B.nprob, "sum_n": int(B.n.sum()), "sum_np": int((B.n.astype(np.int64) * B.p).sum()),
+           "passes": passes, "converged": conv, "iters_max": int(its.max()), "iters_mean": float(its.mean()),
+           "tiles": tuned, "generation_s": gen_s},
+          "df64 blocks (float32 pairs), float32 operator entries, df64 p x p step",
+          {"baseline": {"plain_one_at_a_time_ms_est": est,
+                        "sample": f"{sample} problems solved one after another with gsi_solve "
+                                  f"({plain_ms:.0f} ms, iterations {plain_its}), scaled by {B.nprob}/{sample}",
+                        "speedup": est / value},
+           "clocks": clk, "gpu_launches": launches})
+
+
+def run_warm(args):
+    """Learned warm start on the diffusion family (24 x 24 grid, lowest p = 4
+    modes via -A, 8 x 8 coarse grid, network 16 -> 256 -> 256 -> 256): labels
+    from 384 plain solves (the converged ones), 1500 Adam steps, then each of
+    16 held-out operators solved on its own from the random and from the
+    learned start (network inference and prolongation counted in the
+    learned start's time)."""
+    import numpy as np
+    import torch
+    from paper_2306_10379_gb300 import build, gsi, inputs as I
+    build.build()
+    nx, p, nc, cap, hidden = 24, 4, 8, 8000, 256
+    m = nc * nc
+    # S = P^T P by the library's own prolongation and restriction of the identity
+    eye = torch.eye(m, dtype=torch.float32, device="cuda").reshape(1, m, m).contiguous()
+    Sh = gsi.restrict(gsi.prolong(eye, nc, nx, m).contiguous(), nc, nx, m)[0].double().cpu().numpy()
+    rows, cols = np.nonzero(Sh)
+    Sd = (torch.tensor(np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=m))]).astype(np.int64),
+                       device="cuda"),
+          torch.tensor(cols.astype(np.int32), device="cuda"), torch.tensor(Sh[rows, cols], device="cuda"))
+
+    def family(nops, seed, X0=None):
+        B, xs = I.diffusion_batch(nops, seed, nx, p)
+        b = gsi.Batch(B, method="cg", which=-1, tol=1e-8, max_iters=cap)
+        if X0 is not None:
+            b.restart(X0)
+        ms, _ = _timed(torch, lambda: b.solve(check=False), 1)
+        info = [b.info(i) for i in range(nops)]
+        U = np.stack([b.basis(i, evals=False)[0] for i in range(nops)])
+        b.close()
+        return B, xs.astype(np.float32), U, info, ms
+
+    _, xtr, Utr, itr, _ = family(384, I.SEED_BASE + 1000)
+    keep = np.flatnonzero([f["converged"] == 1 for f in itr])
+    Bt = gsi.restrict(torch.tensor(Utr[keep], device="cuda"), nc, nx, p).contiguous()
+    xd = torch.tensor(xtr[keep], device="cuda")
+    net = gsi.MLP(16, hidden, m * p, gsi.MLP.flatten(I.mlp_init(16, hidden, m * p, I.SEED_BASE + 7)),
+                  max_batch=32)
+    rng = np.random.default_rng(0)
+    t0 = time.time()
+    losses = []
+    for step in range(1500):
+        idx = torch.tensor(rng.choice(len(keep), 32, replace=False), device="cuda")
+        losses.append(net.train_step(xd[idx].contiguous(), Sd, Bt[idx].contiguous(), m, p,
+                                     1e-3 if step < 1100 else 3e-4))
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    # held-out operators: the network's start (inference and prolongation)
+    # and each operator's own solve from the random and from the learned start
+    Bte, xte = I.diffusion_batch(16, I.SEED_BASE + 5000, nx, p)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = gsi.launch_count()
+    torch.cuda.synchronize()
+    ti = time.perf_counter()
+    out = torch.empty((16, m * p), dtype=torch.float32, device="cuda")
+    net.forward(torch.tensor(xte.astype(np.float32), device="cuda"), out)
+    X0 = gsi.prolong(out.view(16, m, p).contiguous(), nc, nx, p)
+    torch.cuda.synchronize()
+    infer_ms = (time.perf_counter() - ti) * 1e3
+    res = {"random": [], "learned": []}
+    for i in range(16):
+        for kind in ("random", "learned"):
+            start = Bte.X0s[i] if kind == "random" else X0[i].contiguous()
+            s = gsi.Solver(Bte.mats[i], p, start, method="cg", which=-1, tol=1e-8, max_iters=cap)
+            ms, info = _timed(torch, lambda: s.solve(), 1)
+            s.close()
+            res[kind].append((ms, info["iters"], info["matvecs"], info["converged"]))
+    clk = clocks.stop()
+    launches = gsi.launch_count() - l0
+    net.close()
+    r = np.array(res["random"])
+    w = np.array(res["learned"])
+    value = float(w[:, 0].sum()) + infer_ms
+    ms_random = float(r[:, 0].sum())
+    itr_r, itr_w = r[:, 1], w[:, 1]
+    _line(args, "ms to rel. residual 1e-8 (learned vs random start)", value,
+          {"workload": "diffusion -div(kappa grad u), 24x24 grid, lowest p=4 modes (via -A), 16 held-out "
+                       "operators, batched RCG to 1e-8 (iterations capped at 8000)",
+           "training": f"{len(keep)} converged of 384 plain solves, 1500 Adam steps ({train_s:.1f} s), "
+                       f"loss {np.mean(losses[:20]):.3f} -> {np.mean(losses[-20:]):.3f}",
+           "iters_learned": {"mean": float(itr_w.mean()), "median": float(np.median(itr_w))},
+           "matvecs_learned": int(w[:, 2].sum()), "converged_learned": int(w[:, 3].sum()),
+           "inference_prolongation_ms": infer_ms,
+           "timing": "sum over the 16 operators of each one's own solve (gsi_solve)"},
+          "bf16 tensor-core MLP, df64 solve",
+          {"baseline": {"random_start_ms": ms_random,
+                        "iters_random": {"mean": float(itr_r.mean()), "median": float(np.median(itr_r))},
+                        "matvecs_random": int(r[:, 2].sum()), "converged_random": int(r[:, 3].sum()),
+                        "speedup": ms_random / value},
+           "clocks": clk, "gpu_launches": launches})
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "fd3d":
+        return {"dense": run_dense, "batched": run_batched, "warm": run_warm}[args.workload](args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -295,6 +519,15 @@ def main():
                 "launch_ms": avg_ms, "alg_bytes_per_launch": bytes_per,
                 "classes": {k: {"launches": v["launches"], "ms_total": v["ms"]} for k, v in prof.items()}}
 
+    # the block matvec (SpMM) against the HBM roofline
+    sp = prof.get("spmm", {"launches": 0})
+    spmm_roofline = None
+    if sp["launches"]:
+        sp_ms = sp["ms"] / sp["launches"]
+        sp_b = sp["bytes"] / sp["launches"]
+        spmm_roofline = {"bound": "hbm", "achieved": sp_b / (sp_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": sp_b / (sp_ms * 1e-3) / 1e9 / hbm_peak,
+                         "launch_ms": sp_ms, "alg_bytes_per_launch": sp_b}
     out = {
         "metric": metric_name(), "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -308,6 +541,7 @@ def main():
                    "rel_residual": info["rel_residual"],
                    "ritz_max_rel_err": float(max(abs(ev - lam[:p]) / lam[:p]))},
         "roofline": roofline,
+        "spmm_roofline": spmm_roofline,
         "clocks": clk,
         "gpu_launches": launches,
     }

@@ -584,17 +584,10 @@ def bf16_round(x):
 
 
 def mlp_init(din, hidden, dout, seed):
-    """He-style initial weights from the shared Philox normals: W ~ N(0, 2/fan_in)
-    (last layer N(0, 1/fan_in)), zero biases. Returns a dict of float32 arrays."""
-    from paper_2306_10379_gb300.inputs import gaussian
-    sizes = [("W1", hidden, din, 2.0), ("W2", hidden, hidden, 2.0), ("W3", dout, hidden, 1.0)]
-    prm = {}
-    for k, (name, r, c, g) in enumerate(sizes):
-        prm[name] = (gaussian(r * c, seed, stream=20 + k).reshape(r, c) * np.sqrt(g / c)).astype(np.float32)
-    prm["b1"] = np.zeros(hidden, np.float32)
-    prm["b2"] = np.zeros(hidden, np.float32)
-    prm["b3"] = np.zeros(dout, np.float32)
-    return prm
+    """The network's seeded initial weights (a seeded input, shared with the
+    library's callers: paper_2306_10379_gb300.inputs.mlp_init)."""
+    from paper_2306_10379_gb300.inputs import mlp_init as _init
+    return _init(din, hidden, dout, seed)
 
 
 def mlp_forward(prm, x, bf16=True):

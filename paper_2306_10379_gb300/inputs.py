@@ -323,3 +323,18 @@ def diffusion_batch(nops: int, seed: int, nx: int, p: int) -> tuple:
     mats = [diffusion_fd(nx, xi, f32=True) for xi in xis]
     X0s = [start_block(nx * nx, p, seed + 2_000_003 + i) for i in range(nops)]
     return ERBatch([nx * nx] * nops, [p] * nops, mats, X0s), np.stack([x.ravel() for x in xis])
+
+
+def mlp_init(din: int, hidden: int, dout: int, seed: int) -> dict:
+    """Seeded initial weights of the warm-start network: W ~ N(0, 2/fan_in)
+    for the two hidden layers, N(0, 1/fan_in) for the output layer (Philox
+    normals, streams 20..22), zero biases; float32 arrays W1 (hidden x din),
+    b1, W2 (hidden x hidden), b2, W3 (dout x hidden), b3."""
+    sizes = [("W1", hidden, din, 2.0), ("W2", hidden, hidden, 2.0), ("W3", dout, hidden, 1.0)]
+    prm = {}
+    for k, (name, r, c, g) in enumerate(sizes):
+        prm[name] = (gaussian(r * c, seed, stream=20 + k).reshape(r, c) * np.sqrt(g / c)).astype(np.float32)
+    prm["b1"] = np.zeros(hidden, np.float32)
+    prm["b2"] = np.zeros(hidden, np.float32)
+    prm["b3"] = np.zeros(dout, np.float32)
+    return prm
