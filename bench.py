@@ -35,8 +35,12 @@ WARMUP_ITERS = 200
 # DRAM bytes per launch from one ncu capture of the kernel (profiles/), scaled
 # to the bench size by the rows processed (traffic grows in proportion).
 NCU_TRAFFIC = {
-    # oz_gram_kernel at n = 524,288, p = 64: read 537.1 MB + write 3.7 MB
-    "gram": {"n": 524288, "p": 64, "bytes": 537.148416e6 + 3.734272e6},
+    # DRAM read + write per launch at n = 512,000, p = 64 (profiles/digit_kernels_fd3d80_p64.md),
+    # averaged over one iteration's launches of the class
+    "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.2e6 + 3.8e6) + 3 * (524.5e6 + 3.6e6)) / 5},
+    "blockmul": {"n": 512000, "p": 64, "bytes": ((787.8e6 + 248.4e6) + (787.3e6 + 246.8e6)
+                                                  + 2 * (524.5e6 + 233.3e6)) / 4},
+    "spmm": {"n": 512000, "p": 64, "bytes": 308.8e6 + 229.4e6},
 }
 
 
@@ -527,7 +531,9 @@ def main():
         sp_b = sp["bytes"] / sp["launches"]
         spmm_roofline = {"bound": "hbm", "achieved": sp_b / (sp_ms * 1e-3) / 1e9, "peak": hbm_peak,
                          "unit": "GB/s", "frac": sp_b / (sp_ms * 1e-3) / 1e9 / hbm_peak,
-                         "launch_ms": sp_ms, "alg_bytes_per_launch": sp_b}
+                         "launch_ms": sp_ms, "alg_bytes_per_launch": sp_b,
+                         "traffic": (NCU_TRAFFIC["spmm"]["bytes"] * n / NCU_TRAFFIC["spmm"]["n"]
+                                     if p == NCU_TRAFFIC["spmm"]["p"] else None)}
     out = {
         "metric": metric_name(), "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
