@@ -336,7 +336,9 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
           if (C + e2 >= p) continue;
           float2 y = v[e2];
           const int64_t idx = R * p + C + e2;
-          for (int m = 0; m < a.ne; ++m) y = df_add(y, df_mul(a.ce[m], a.E[m][idx]));
+#pragma unroll
+          for (int m = 0; m < 2; ++m)  // constant indices keep the arguments in parameter space
+            if (m < a.ne) y = df_add(y, df_mul(a.ce[m], a.E[m][idx]));
           if (a.dot_self) dacc0 = df_add(dacc0, df_mul(y, y));
           if (a.dot_with) dacc1 = df_add(dacc1, df_mul(y, a.dot_with[idx]));
           a.out[idx] = y;
@@ -566,6 +568,21 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
                    : "memory");
     }
     load_tile(tile + gridDim.x);  // registers only: the digit planes are in use
+    // row-wise epilogue (NC = 64 columns inside the block, even p): warp w
+    // owns rows w + 16 k (k < 8), lane l columns 2l, 2l + 1; the first row's
+    // elementwise operands are fetched now, each later row's one row ahead
+    const bool rowwise = NC == 64 && col0 + 64 <= p && (p & 1) == 0;
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0;
+    auto fetch_row = [&](int k) {
+      const int64_t R = r0 + warp + 16 * k;
+      if (R < n) {
+        const int64_t idx = R * p + col0 + 2 * lane;
+        if (a.ne > 0) q0 = *reinterpret_cast<const float4*>(a.E[0] + idx);
+        if (a.ne > 1) q1 = *reinterpret_cast<const float4*>(a.E[1] + idx);
+        if (a.dot_with) q2 = *reinterpret_cast<const float4*>(a.dot_with + idx);
+      }
+    };
+    if (rowwise) fetch_row(0);
     const bool done = tc_wait(mb, phase);
     phase ^= 1u;
     if (__syncthreads_or(!done)) {
@@ -576,10 +593,11 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     // (c) epilogue, part 1: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its
     // rows) and the column quarter w / 4, 4 columns at a time; the combined
     // and scaled products go to shared memory (the digit planes are free once
-    // the products completed: 128 (NC + 1) float2 <= 7 * 128 * K16 bf16 for
-    // NC = K16 >= 16), row stride NC + 1 float2 (two wavefronts per warp store)
+    // the products completed: 128 (NC + 2) float2 <= 7 * 128 * K16 bf16 for
+    // NC <= K16, K16 >= 16), row stride NC + 2 float2 so that every row starts
+    // on 16 bytes (16-byte stores and loads, four wavefronts per warp access)
     float2* stage = reinterpret_cast<float2*>(Ad);
-    const int ss = NC + 1;
+    const int ss = NC + 2;
     {
       const int row = 32 * (warp & 3) + lane;
       const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -590,27 +608,59 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
         for (int g = 0; g < ND; ++g) tc_ld4(v[g], lanes + (uint32_t)(g * NC + c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
+        float2 y[4];
+#pragma unroll
         for (int e2 = 0; e2 < 4; ++e2) {
           float S[ND];
 #pragma unroll
           for (int g = 0; g < ND; ++g) S[g] = __uint_as_float(v[g][e2]);
           const float2 w = combine_groups<ND>(S);
           const int sc = Er[row] + Fs[c0 + e2] - 14;
-          float2 y;
           if (sc >= -126) {
             const float f = exp2i(sc);
-            y = make_float2(w.x * f, w.y * f);
+            y[e2] = make_float2(w.x * f, w.y * f);
           } else {
             const float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
-            y = make_float2(w.x * f1 * f2, w.y * f1 * f2);
+            y[e2] = make_float2(w.x * f1 * f2, w.y * f1 * f2);
           }
-          stage[row * ss + c0 + e2] = y;
         }
+        float4* d4 = reinterpret_cast<float4*>(stage + row * ss + c0);
+        d4[0] = make_float4(y[0].x, y[0].y, y[1].x, y[1].y);
+        d4[1] = make_float4(y[2].x, y[2].y, y[3].x, y[3].y);
       }
     }
     __syncthreads();
     // part 2: row-contiguous pass over the tile: elementwise terms, dots and
     // the store, coalesced
+    if (rowwise) {
+#pragma unroll 1
+      for (int k = 0; k < TC_M / 16; ++k) {
+        const int rr = warp + 16 * k;
+        const int64_t R = r0 + rr;
+        const float4 e0 = q0, e1 = q1, w2 = q2;
+        if (k + 1 < TC_M / 16) fetch_row(k + 1);
+        if (R >= n) continue;
+        const float4 sv = *reinterpret_cast<const float4*>(stage + rr * ss + 2 * lane);
+        float2 y0 = make_float2(sv.x, sv.y), y1 = make_float2(sv.z, sv.w);
+        if (a.ne > 0) {
+          y0 = df_add(y0, df_mul(a.ce[0], make_float2(e0.x, e0.y)));
+          y1 = df_add(y1, df_mul(a.ce[0], make_float2(e0.z, e0.w)));
+        }
+        if (a.ne > 1) {
+          y0 = df_add(y0, df_mul(a.ce[1], make_float2(e1.x, e1.y)));
+          y1 = df_add(y1, df_mul(a.ce[1], make_float2(e1.z, e1.w)));
+        }
+        if (a.dot_self) {
+          dacc0 = df_add(dacc0, df_mul(y0, y0));
+          dacc0 = df_add(dacc0, df_mul(y1, y1));
+        }
+        if (a.dot_with) {
+          dacc1 = df_add(dacc1, df_mul(y0, make_float2(w2.x, w2.y)));
+          dacc1 = df_add(dacc1, df_mul(y1, make_float2(w2.z, w2.w)));
+        }
+        *reinterpret_cast<float4*>(a.out + R * p + col0 + 2 * lane) = make_float4(y0.x, y0.y, y1.x, y1.y);
+      }
+    } else
     for (int e = tid; e < TC_M * NC; e += TC_THREADS) {
       const int rr = e / NC, cc = e - rr * NC;
       const int64_t R = r0 + rr;
@@ -618,7 +668,9 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
       if (R >= n || C >= p) continue;
       float2 y = stage[rr * ss + cc];
       const int64_t idx = R * p + C;
-      for (int m = 0; m < a.ne; ++m) y = df_add(y, df_mul(a.ce[m], a.E[m][idx]));
+#pragma unroll
+      for (int m = 0; m < 2; ++m)  // constant indices keep the arguments in parameter space
+        if (m < a.ne) y = df_add(y, df_mul(a.ce[m], a.E[m][idx]));
       if (a.dot_self) dacc0 = df_add(dacc0, df_mul(y, y));
       if (a.dot_with) dacc1 = df_add(dacc1, df_mul(y, a.dot_with[idx]));
       a.out[idx] = y;
