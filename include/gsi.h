@@ -309,13 +309,15 @@ gsi_status gsi_oz_dense_apply(int64_t n, int32_t p, const float* A, const float*
 gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, const float* V,
                                int32_t sym, double* G, void* stream);
 
-/* Which tensor-core kernels the digit-split products use: 0 (default) the
- * tcgen05 kernels where they are the faster ones (block products and
- * symmetric Grams with p <= 64), 1 the mma.sync kernels everywhere, 2 the
- * tcgen05 kernels wherever they apply (all products with p, q <= 64). All
- * give identical results (the digit-pair sums are exact integers); the
- * switch exists to compare them. Process-wide; the environment variable
- * GSI_TENSOR_PATH=mma or =tcgen05 selects 1 or 2 before the first product. */
+/* Which tensor-core kernels the digit-split products use: 0 (default) and 2
+ * the tcgen05 kernels wherever they apply (all products with p, q <= 64),
+ * 1 the mma.sync kernels everywhere. Block products are identical on both
+ * (same digits, exact integer digit-pair sums, same combination order).
+ * Grams agree to float64-class accuracy but not bit for bit: the tcgen05
+ * Gram takes its column exponents over 256-row (U == V) or 128-row chunks,
+ * the mma.sync Gram over 64-row chunks. The switch exists to compare them.
+ * Process-wide; the environment variable GSI_TENSOR_PATH=mma or =tcgen05
+ * selects 1 or 2 before the first product. */
 gsi_status gsi_set_tensor_path(int32_t path);
 int32_t gsi_tensor_path(void);
 

@@ -8,7 +8,8 @@
 // Block data is df64 (float2 = hi, lo). Every operand is cut into ND = 7
 // signed "digits" d_i in [-128, 128] on a fixed-point grid set by a power of
 // two per row (gemm, left operand), per column (p x p right operand) or per
-// column and 64-row chunk (gram):
+// column and row chunk (gram: 64 rows in the mma.sync kernel, 256 or 128 in
+// the tcgen05 kernel):
 //   x = 2^(E-7) * sum_{i<7} d_i 2^(-7 i)   (truncation below 2^(E-49)).
 // Digits are exact in bf16, products of two digits are exact in fp32, and the
 // 28 digit pairs (i + i' <= 6) are summed per "group" g = i + i' in fp32
@@ -26,10 +27,10 @@ namespace gsi {
 
 constexpr int ND = 7;
 
-// 0: tcgen05 kernels where they are the faster ones (block products and
-// symmetric Grams with p <= 64), 1: mma.sync kernels only, 2: tcgen05
-// kernels wherever they apply (set by gsi_set_tensor_path, or by
-// GSI_TENSOR_PATH=mma / =tcgen05 at the first product)
+// 0 and 2: tcgen05 kernels wherever they apply (block products with
+// p <= 64 per 64-column slice, Grams with p, q <= 64), 1: mma.sync kernels
+// only (set by gsi_set_tensor_path, or by GSI_TENSOR_PATH=mma / =tcgen05 at
+// the first product)
 static int g_tensor_path = -1;
 int tensor_path() {
   if (g_tensor_path < 0) {
@@ -607,7 +608,6 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
 #pragma unroll
         for (int g = 0; g < ND; ++g) tc_ld4(v[g], lanes + (uint32_t)(g * NC + c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
         float2 y[4];
 #pragma unroll
         for (int e2 = 0; e2 < 4; ++e2) {
@@ -893,33 +893,70 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
 
 // ---------------------------------------------------------------------------
 // oz_gram on the 5th-generation tensor cores, for p, q <= 64 and the 7-digit
-// split: the same 64-row chunks, per-chunk column exponents, digits and df64
-// accumulation as oz_gram_kernel (identical partial sums), with the 28
-// digit-pair products issued by one thread as M = 64, N = 64, K = 16 tcgen05
-// MMAs into 7 tensor-memory group accumulators. Output row i of an M = 64
-// product sits in TMEM lane 32 (i / 16) + i % 16. With U == V (sym) the
-// digits are cut once.
+// split. Rows go in exponent chunks of EC rows (256 for U == V, 128
+// otherwise), staged raw in shared memory by cp.async; the column exponents
+// are taken over the whole chunk, and the chunk's digit-pair products are
+// summed in tensor memory over its sub-chunks of SK rows (32, resp. 16) before
+// one df64 combination per chunk. The group sums stay exact integers: per row
+// |d_0 d_0| <= 2^14 and every other digit product is at most 128 * 72, so even
+// the seven pairs of group 6 sum to less than 2^24 over 256 rows.
+//
+// The products are M = 128, N = 64 MMAs whose A operand stacks two
+// consecutive digit planes of U, [U_2m; U_2m+1] (the planes are adjacent in
+// shared memory, so this is one K-major operand of 128 rows). With B = V_j
+// the top half (TMEM lanes 0..63) gets U_2m^T V_j, group 2m + j, and the
+// bottom half (lanes 64..127) U_2m+1^T V_j, group 2m + 1 + j, both in the
+// accumulator block h = 2m + j. So block h holds the even-digit part of
+// group h in its top lanes and the odd-digit part of group h + 1 in its
+// bottom lanes (block 6's bottom half, "group 7", is never read); 16 MMAs per
+// 16 rows instead of 28. The two parts are combined separately (each an
+// exact integer sum) and added once at the end of the kernel.
+//
+// Digit planes are double-buffered: sub-chunk s + 1 is cut while the tensor
+// core works on sub-chunk s (one mbarrier per buffer). Sixteen worker warps
+// stage, cut and combine; a seventeenth warp only issues the products, so
+// that the issue never holds up a worker at the next barrier.
 // ---------------------------------------------------------------------------
-constexpr int TG_KC = 64;
-constexpr int TG_THREADS = 512;
+constexpr int TG_WORKERS = 512;
+constexpr int TG_THREADS = TG_WORKERS + 32;
+constexpr int TG_RS = 66;              // raw row stride in float2 (528 B: rows on 16 B)
+constexpr int TG_RAW_ROWS = 256;       // U == V: 256 rows of U; else 128 of U, then 128 of V
+constexpr uint32_t TG_DBUF = 32768;    // one digit buffer (A planes, B planes or pad)
 
 size_t oz_gram_tc_smem() {
-  return (size_t)2 * ND * 64 * TG_KC * 2 + 8 * 128 * sizeof(float) + 128 * sizeof(int) + 64;
+  return (size_t)TG_RAW_ROWS * TG_RS * sizeof(float2) + 2 * TG_DBUF + 8 * 64 * sizeof(float) +
+         128 * sizeof(int) + 64;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+
+template <bool SYM>
 __global__ void __launch_bounds__(TG_THREADS, 1)
 oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
-                  int sym, float2* part) {
+                  int vec16, float2* part) {
+  constexpr int EC = SYM ? 256 : 128, SK = SYM ? 32 : 16, NSUB = EC / SK;
+  constexpr uint32_t plane = 64u * SK * 2;  // one digit plane: 64 columns x SK rows, bf16
   extern __shared__ __align__(16) unsigned char tg_smem[];
-  const uint32_t plane = 64 * TG_KC * 2;
-  unsigned char* Ad = tg_smem;
-  unsigned char* Bd = Ad + ND * plane;
-  float* cmx = reinterpret_cast<float*>(Bd + ND * plane);  // [8][128] partial column maxima
-  int* Eu = reinterpret_cast<int*>(cmx + 8 * 128);
+  float2* raw = reinterpret_cast<float2*>(tg_smem);
+  unsigned char* dig = tg_smem + (size_t)TG_RAW_ROWS * TG_RS * sizeof(float2);
+  float* cmx = reinterpret_cast<float*>(dig + 2 * TG_DBUF);  // [8][64] partial column maxima
+  int* Eu = reinterpret_cast<int*>(cmx + 8 * 64);
   int* Ev = Eu + 64;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Ev + 64);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Ev + 64);     // one per digit buffer
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool issuer = warp == TG_WORKERS / 32;
+  // the pad plane after the 7 planes of U (U == V) is read by the bottom half
+  // of the [U_6; U_7] operand, whose products land in the unused "group 7"
+  if (SYM && !issuer)
+    for (int e = tid; e < 2 * (int)(plane / 16); e += TG_WORKERS) {
+      const int b = e / (int)(plane / 16), o = e - b * (int)(plane / 16);
+      *reinterpret_cast<uint4*>(dig + b * TG_DBUF + 7 * plane + 16 * o) = make_uint4(0u, 0u, 0u, 0u);
+    }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
                  "r"(TC_TMEM_COLS));
@@ -927,147 +964,207 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + 1)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
-  const uint32_t abase = smem_addr(Ad), bbase = smem_addr(sym ? Ad : Bd), mb = smem_addr(mbar);
-  const int* Evv = sym ? Eu : Ev;
-  // this thread's outputs: row i = 16 (warp % 4) + lane (lanes < 16), columns
-  // 16 (warp / 4) + 0..15
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
+  const uint32_t dbase = smem_addr(dig);
+  const uint32_t mb0 = smem_addr(mbar), mb1 = smem_addr(mbar + 1);
+  uint32_t ph0 = 0u, ph1 = 0u;  // phases of the two buffers' barriers
+  const int* Evv = SYM ? Eu : Ev;
+  // combine: worker warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. output
+  // row a = 32 (w % 2) + lane of the top (w % 4 < 2) or bottom half, columns
+  // 16 (w / 4) .. + 15
+  const int quarter = warp & 3, arow = 32 * (quarter & 1) + lane, cb = 16 * ((warp >> 2) & 3);
+  const bool top = quarter < 2;
   float2 res[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) res[e] = make_float2(0.f, 0.f);
-  const int orow = 16 * (warp & 3) + (lane & 15), cbase = 16 * (warp >> 2);
-  uint32_t phase = 0;
   bool failed = false;
-  const int64_t nchunks = (n + TG_KC - 1) / TG_KC;
-  // thread <-> column c and the chunk rows 2 rp + h + 16 k (k < 4, h < 2);
-  // the next chunk's values are loaded while the current products run
-  const int c = tid & 63, rp = tid >> 6;
-  float2 xu[8], xv[8];
-  auto load_chunk = [&](int64_t chunk) {
-    const int64_t rb = chunk * TG_KC;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t R = rb + 16 * k + 2 * rp + h;
-        const bool ok = chunk < nchunks && R < n;
-        xu[2 * k + h] = (ok && c < p) ? U[R * p + c] : make_float2(0.f, 0.f);
-        if (!sym) xv[2 * k + h] = (ok && c < q) ? V[R * q + c] : make_float2(0.f, 0.f);
+  const int64_t nchunks = (n + EC - 1) / EC;
+
+  // raw rows of chunk ch (workers): U rows (256, or 128 then V's 128),
+  // zero-filled outside the matrix
+  auto stage = [&](int64_t ch) {
+    const int64_t r0 = ch * EC;
+    if (vec16) {
+      for (int e = tid; e < TG_RAW_ROWS * 32; e += TG_WORKERS) {
+        const int row = e >> 5, c = 2 * (e & 31);
+        const bool isv = !SYM && row >= 128;
+        const int64_t R = r0 + (isv ? row - 128 : row);
+        const int ld = isv ? q : p;
+        const float2* src = isv ? V : U;
+        const bool ok = R < n && c < ld;
+        cp_async16(raw + row * TG_RS + c, src + (ok ? R * ld + c : 0), ok);
       }
+    } else {
+      for (int e = tid; e < TG_RAW_ROWS * 64; e += TG_WORKERS) {
+        const int row = e >> 6, c = e & 63;
+        const bool isv = !SYM && row >= 128;
+        const int64_t R = r0 + (isv ? row - 128 : row);
+        const int ld = isv ? q : p;
+        const float2* src = isv ? V : U;
+        const bool ok = R < n && c < ld;
+        cp_async8(raw + row * TG_RS + c, src + (ok ? R * ld + c : 0), ok);
+      }
+    }
+    cp_async_commit();
   };
-  load_chunk(blockIdx.x);
-  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    // (a) the chunk's column maxima of |hi|
-    float mu = 0.f, mv = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      mu = fmaxf(mu, fabsf(xu[k].x));
-      if (!sym) mv = fmaxf(mv, fabsf(xv[k].x));
-    }
-    cmx[rp * 128 + c] = mu;
-    cmx[rp * 128 + 64 + c] = mv;
+
+  // digit item of this worker (one per sub-chunk): column c, rows
+  // 4 qd .. 4 qd + 3 of the sub-chunk, of U or (isv) of V. Lanes cover 8
+  // columns x 2 quads x 2 row octets, so a warp's 8-byte stores fill 2 x 32
+  // banks and its raw loads 2 x 32 banks.
+  const bool isv = !SYM && tid >= 256;
+  const int loc = SYM ? tid : (tid & 255);
+  const int ic = 8 * ((loc >> 5) & 7) + (lane & 7);
+  const int iq = 2 * (((lane >> 4) & 1) + 2 * (loc >> 8)) + ((lane >> 3) & 1);
+  const int irow = (isv ? 128 : 0) + 4 * iq;
+
+  if (!issuer && (int64_t)blockIdx.x < nchunks) stage(blockIdx.x);
+  for (int64_t ch = blockIdx.x; ch < nchunks && !failed; ch += gridDim.x) {
+    if (!issuer) cp_async_wait_all();
     __syncthreads();
-    if (tid < 128) {
+    // (a) column maxima of |hi| over the chunk: thread -> column c, 32 rows
+    // of raw row group g (g < 4: U, else V when U != V)
+    if (!issuer) {
+      const int c = tid & 63, g = tid >> 6;
+      float mx = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) mx = fmaxf(mx, fabsf(raw[(32 * g + k) * TG_RS + c].x));
+      cmx[g * 64 + c] = mx;
+    }
+    __syncthreads();
+    if (tid < (SYM ? 64 : 128)) {
+      const int c = tid & 63, g0 = (tid < 64) ? 0 : 4, ng = SYM ? 8 : 4;
       float m = 0.f;
-      for (int g = 0; g < 8; ++g) m = fmaxf(m, cmx[g * 128 + tid]);
-      if (tid < 64) Eu[tid] = exponent_above(m);
-      else Ev[tid - 64] = exponent_above(m);
+      for (int g = g0; g < g0 + ng; ++g) m = fmaxf(m, cmx[g * 64 + c]);
+      if (tid < 64) Eu[c] = exponent_above(m);
+      else Ev[c] = exponent_above(m);
     }
     __syncthreads();
-    // (b) digits into the K-major planes: element (row r, column c) of the
-    // chunk is entry (m = c, k = r); pairs of rows pack into one word
-    {
-      const int Ec = Eu[c];
+    // (b) sub-chunks: cut into digit buffer s % 2, products on the tensor core
+    for (int s = 0; s < NSUB; ++s) {
+      const int buf = s & 1;
+      bool ok = true;
+      if (s >= 2) {  // the products of sub-chunk s - 2 read this buffer
+        if (!issuer) ok = tc_wait(buf ? mb1 : mb0, buf ? ph1 : ph0);
+        if (buf) ph1 ^= 1u;
+        else ph0 ^= 1u;
+      }
+      if (!issuer) {
+        unsigned char* dst = dig + buf * TG_DBUF + (isv ? 7 * plane : 0);
+        const int r = irow + s * SK;
+        const int E = (isv ? Ev : Eu)[ic];
+        float d[4][ND];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int r = 16 * k + 2 * rp;
-        float d0[ND], d1[ND];
-        digitsN<ND>(xu[2 * k].x, xu[2 * k].y, Ec, d0);
-        digitsN<ND>(xu[2 * k + 1].x, xu[2 * k + 1].y, Ec, d1);
+        for (int t = 0; t < 4; ++t) {
+          const float2 x = raw[(r + t) * TG_RS + ic];
+          digitsN<ND>(x.x, x.y, E, d[t]);
+        }
 #pragma unroll
         for (int i = 0; i < ND; ++i)
-          *reinterpret_cast<uint32_t*>(Ad + i * plane + tc_off(c, r, TG_KC)) = pack_bf16x2(d0[i], d1[i]);
+          *reinterpret_cast<uint2*>(dst + i * plane + tc_off(ic, 4 * iq, SK)) =
+              make_uint2(pack_bf16x2(d[0][i], d[1][i]), pack_bf16x2(d[2][i], d[3][i]));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      if (!sym) {
-        const int Fc = Ev[c];
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (issuer) {
+        if (lane == 0) {
+          const uint32_t ab = dbase + buf * TG_DBUF, bb = SYM ? ab : ab + 7 * plane;
+          const uint64_t da = tc_desc(ab, SK), db = tc_desc(bb, SK);
+          const uint32_t acc0 = s > 0 ? 1u : 0u;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int r = 16 * k + 2 * rp;
-          float d0[ND], d1[ND];
-          digitsN<ND>(xv[2 * k].x, xv[2 * k].y, Fc, d0);
-          digitsN<ND>(xv[2 * k + 1].x, xv[2 * k + 1].y, Fc, d1);
+          for (int m = 0; m < 4; ++m)
 #pragma unroll
-          for (int i = 0; i < ND; ++i)
-            *reinterpret_cast<uint32_t*>(Bd + i * plane + tc_off(c, r, TG_KC)) = pack_bf16x2(d0[i], d1[i]);
+            for (int j = 0; j < ND - 2 * m; ++j)
+#pragma unroll
+              for (int ks = 0; ks < SK / 16; ++ks)
+                tc_mma(tmem + (uint32_t)((2 * m + j) * 64), da + ((2 * m * plane + ks * 256) >> 4),
+                       db + ((j * plane + ks * 256) >> 4), idesc, (m > 0 || ks > 0) ? 1u : acc0);
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           buf ? mb1 : mb0)
+                       : "memory");
         }
+        __syncwarp();
+      } else if (s == NSUB - 1 && ch + gridDim.x < nchunks) {
+        stage(ch + gridDim.x);  // raw rows are free
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // (c) the 28 digit-pair products, grouped by g = i + j
-    if (tid == 0) {
-      for (int g = 0; g < ND; ++g)
-        for (int i = 0; i <= g; ++i)
-          for (int ks = 0; ks < TG_KC / 16; ++ks)
-            tc_mma(tmem + (uint32_t)(g * 64), tc_desc(abase + i * plane + ks * 256, TG_KC),
-                   tc_desc(bbase + (g - i) * plane + ks * 256, TG_KC), idesc, (i > 0 || ks > 0) ? 1u : 0u);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                   : "memory");
+    if (failed) break;
+    // (c) the last two sub-chunks' products, then the combination
+    bool ok = true;
+    if (!issuer) {
+      ok = tc_wait(mb0, ph0);
+      ok = tc_wait(mb1, ph1) && ok;
     }
-    load_chunk(ch + gridDim.x);  // registers only: the digit planes are in use
-    const bool done = tc_wait(mb, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!done)) {
+    ph0 ^= 1u;
+    ph1 ^= 1u;
+    if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // (d) group sums back from tensor memory, combined and scaled per chunk
-    {
-      const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    if (!issuer) {
+      const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll
       for (int c0 = 0; c0 < 16; c0 += 4) {
         uint32_t v[ND][4];
 #pragma unroll
-        for (int g = 0; g < ND; ++g) tc_ld4(v[g], lanes + (uint32_t)(g * 64 + cbase + c0));
+        for (int h = 0; h < ND; ++h)
+          if (top || h < ND - 1) tc_ld4(v[h], lanes + (uint32_t)(h * 64 + cb + c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (lane < 16) {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float S[ND];
+        for (int e = 0; e < 4; ++e) {
+          float S[ND];
 #pragma unroll
-            for (int g = 0; g < ND; ++g) S[g] = __uint_as_float(v[g][e]);
-            const float2 w = combine_groups<ND>(S);
-            const int sc = Eu[orow] + Evv[cbase + c0 + e] - 14;
-            const float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
-            res[c0 + e] = df_add(res[c0 + e], make_float2(w.x * f1 * f2, w.y * f1 * f2));
-          }
+          for (int h = 0; h < ND; ++h) S[h] = __uint_as_float(v[h][e]);
+          // top: sum_h S_h 2^(-7h); bottom: 2^-7 sum_{h<6} S_h 2^(-7h)
+          const float2 w = top ? combine_groups<ND>(S) : combine_groups<ND - 1>(S);
+          const int sc = Eu[arow] + Evv[cb + c0 + e] - 14 - (top ? 0 : 7);
+          const float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
+          res[c0 + e] = df_add(res[c0 + e], make_float2(w.x * f1 * f2, w.y * f1 * f2));
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
+  if (!issuer) cp_async_wait_all();
   if (failed) {
+    // a product that did not complete: count it, wait once more (bounded)
+    // for the tensor core, and report non-finite partial sums
     if (tid == 0) atomicAdd(&g_oz_tc_timeouts, 1);
-    tc_wait(mb, phase ^ 1u);
+    if (!issuer) {
+      tc_wait(mb0, ph0);
+      tc_wait(mb1, ph1);
+    }
 #pragma unroll
     for (int e = 0; e < 16; ++e) res[e] = make_float2(NAN, NAN);
   }
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
-  if (lane < 16) {
+  // odd-digit parts (bottom half) onto the even-digit parts, once per block
+  float2* st = raw;  // 64 x 65 float2
+  if (!issuer && !top) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) st[arow * 65 + cb + e] = res[e];
+  }
+  __syncthreads();
+  if (!issuer && top) {
     float2* out = part + (size_t)blockIdx.x * 4096;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) out[orow * 64 + cbase + e] = res[e];
+    for (int e = 0; e < 16; ++e) out[arow * 64 + cb + e] = df_add(res[e], st[arow * 65 + cb + e]);
   }
 }
 
@@ -1232,11 +1329,14 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
   const int nblk = oz_gram_blocks(p, q, sym);
   const int ns = oz_gram_splits(n, p, q, sym);
   const int tp = tensor_path();
-  if (nd == ND && p <= 64 && q <= 64 && (tp == 2 || (tp == 0 && sym))) {
-    // one 64 x 64 output block; every partial entry is written
+  if (nd == ND && p <= 64 && q <= 64 && tp != 1) {
+    // one 64 x 64 output block; every partial entry is written. 16-byte
+    // copies need even row lengths and 16-byte aligned bases.
+    const bool vec16 = ((p | q) & 1) == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)V & 15) == 0;
     const size_t tsm = oz_gram_tc_smem();
-    GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    oz_gram_tc_kernel<<<ns, TG_THREADS, tsm, st>>>(n, p, q, U, V, sym ? 1 : 0, scratch);
+    auto kern = sym ? oz_gram_tc_kernel<true> : oz_gram_tc_kernel<false>;
+    GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    kern<<<ns, TG_THREADS, tsm, st>>>(n, p, q, U, V, vec16 ? 1 : 0, scratch);
     GSI_LAUNCH_CHECK();
   } else {
     size_t smem = oz_gram_smem(nd);

@@ -102,11 +102,30 @@ def test_oz_gemm_in_place(G):
     assert np.linalg.norm(gsi.from_df(Ed.cpu().numpy()) - (U @ M - E)) <= 1e-13 * np.linalg.norm(U @ M)
 
 
+def _gram_bound(U, V, rows=256):
+    """Error bound of the digit-split Gram: per chunk of `rows` rows every
+    product is cut at 2^-49 of the chunk's column maxima. Chunks of 256 rows
+    bound the 64-row chunks of the mma.sync kernel and the 256/128-row chunks
+    of the tcgen05 kernel alike (a sub-chunk's maxima are at most its
+    chunk's)."""
+    n, p = U.shape
+    chunk_bound = np.zeros((p, V.shape[1]))
+    for r0 in range(0, n, rows):
+        cu = np.abs(U[r0:r0 + rows]).max(0)
+        cv = np.abs(V[r0:r0 + rows]).max(0)
+        chunk_bound += np.outer(cu, cv) * min(rows, n - r0)
+    return 2.0 ** -44 * chunk_bound + 2.0 ** -46 * (np.abs(U).T @ np.abs(V))
+
+
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("n,p,q,sym", [(1, 1, 1, False), (63, 8, 8, True), (65, 8, 3, False),
                                        (10007, 64, 64, True), (10007, 64, 64, False),
                                        (200001, 64, 64, True), (30000, 128, 128, True),
-                                       (30000, 65, 128, False), (5000, 100, 17, False)])
-def test_oz_gram(G, n, p, q, sym):
+                                       (30000, 65, 128, False), (5000, 100, 17, False),
+                                       (4099, 48, 64, False), (1000, 33, 33, True), (777, 33, 17, False)])
+def test_oz_gram(G, n, p, q, sym, path):
+    """Both tensor paths against the oracle's float64 Gram of the same df64
+    values (tcgen05 where p, q <= 64 on path 0; mma.sync on path 1)."""
     torch, gsi = G
     rng = np.random.default_rng(n * 3 + p)
     U = _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-4, 4, (1, p))))
@@ -114,19 +133,67 @@ def test_oz_gram(G, n, p, q, sym):
     Ud = _df_dev(torch, gsi, U)
     Vd = Ud if sym else _df_dev(torch, gsi, V)
     Gm = torch.full((p, q), np.nan, dtype=torch.float64, device="cuda")
-    gsi.oz_gram(Ud, Vd, Gm, sym=sym)
+    gsi.set_tensor_path(path)
+    try:
+        gsi.oz_gram(Ud, Vd, Gm, sym=sym)
+    finally:
+        gsi.set_tensor_path(0)
     got = Gm.cpu().numpy()
     ref = O.gram(U, V)
-    absprod = np.abs(U).T @ np.abs(V)
-    # per 64-row chunk each product is cut at 2^-49 of the chunk column maxima
-    chunk_bound = np.zeros((p, q))
-    for r0 in range(0, n, 64):
-        cu = np.abs(U[r0:r0 + 64]).max(0)
-        cv = np.abs(V[r0:r0 + 64]).max(0)
-        chunk_bound += np.outer(cu, cv) * min(64, n - r0)
-    assert np.all(np.abs(got - ref) <= 2.0 ** -44 * chunk_bound + 2.0 ** -46 * absprod)
+    assert np.all(np.abs(got - ref) <= _gram_bound(U, V))
     if sym:
         assert np.array_equal(got, got.T)
+
+
+def _six_digit_block(rng, n, p):
+    """Entries sum_{i<6} d_i 2^(-7(i+1)) with large positive digits
+    (d_0 in [100, 127], d_1..d_5 in [40, 63]): below 1, 42 significant bits,
+    so exact in df64 and cut into exactly these digits (column exponent 0),
+    with digit-pair group sums near the 2^24 limit over 256 rows. Returned as
+    integers (the value times 2^42) and as float64."""
+    d = np.concatenate([rng.integers(100, 128, (n, p, 1)), rng.integers(40, 64, (n, p, 5))], axis=2)
+    k = np.zeros((n, p), dtype=np.int64)
+    for i in range(6):
+        k = k * 128 + d[:, :, i]
+    return k, k.astype(np.float64) * 2.0 ** -42
+
+
+def _exact_gram(ku, kv):
+    """U^T V exactly for integer blocks below 2^42 (21-bit halves, int64
+    products), returned as Python integers (scaled by 2^84)."""
+    hu, lu = ku >> 21, ku & ((1 << 21) - 1)
+    hv, lv = kv >> 21, kv & ((1 << 21) - 1)
+    hh, hl, lh, ll = hu.T @ hv, hu.T @ lv, lu.T @ hv, lu.T @ lv
+    return [[(int(hh[i, j]) << 42) + ((int(hl[i, j]) + int(lh[i, j])) << 21) + int(ll[i, j])
+             for j in range(ku.shape[1])] for i in range(ku.shape[1])]
+
+
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("n,sym", [(1000, True), (1000, False), (256, True)])
+def test_oz_gram_large_digit_sums_exact(G, n, sym, path):
+    """Digit-pair group sums close to 2^24 (all digits large and positive, 256
+    rows per exponent chunk) must still be summed exactly by the tensor
+    cores: the Gram of these 42-bit entries equals the exact integer Gram to
+    df64 rounding (relative 2^-46; a single lost unit in any group sum would
+    be 2^-22 or more)."""
+    torch, gsi = G
+    rng = np.random.default_rng(1234 + n + sym)
+    p = 64
+    ku, U = _six_digit_block(rng, n, p)
+    kv, V = (ku, U) if sym else _six_digit_block(rng, n, p)
+    assert np.array_equal(gsi.from_df(gsi.to_df(U)), U)  # exact in df64
+    Ud = _df_dev(torch, gsi, U)
+    Vd = Ud if sym else _df_dev(torch, gsi, V)
+    Gm = torch.full((p, p), np.nan, dtype=torch.float64, device="cuda")
+    gsi.set_tensor_path(path)
+    try:
+        gsi.oz_gram(Ud, Vd, Gm, sym=sym)
+    finally:
+        gsi.set_tensor_path(0)
+    got = Gm.cpu().numpy()
+    ex = _exact_gram(ku, kv)
+    rel = max(abs(got[i, j] * 2.0 ** 84 - ex[i][j]) / ex[i][j] for i in range(p) for j in range(p))
+    assert rel <= 2.0 ** -46, rel
 
 
 @pytest.mark.parametrize("n,p", [(5000, 64), (3001, 17), (4000, 128)])
@@ -174,14 +241,18 @@ def test_oz_gemm_tcgen05_equals_mma(G, n, p, fused, ne):
 
 @pytest.mark.parametrize("n,p,q,sym", [(100003, 64, 64, True), (100003, 64, 64, False), (4097, 17, 40, False),
                                        (70, 8, 8, True), (200000, 48, 5, False)])
-def test_oz_gram_tcgen05_equals_mma(G, n, p, q, sym):
-    """The tcgen05 Gram (tensor-memory group accumulators) and the mma.sync one
-    cut the same chunks into the same digits, sum the same exact integer
-    products and accumulate them in the same order: bit-identical Grams."""
+def test_oz_gram_tcgen05_and_mma_agree(G, n, p, q, sym):
+    """The tcgen05 Gram (256/128-row exponent chunks, tensor-memory group
+    sums) and the mma.sync one (64-row chunks) are different roundings of the
+    same exact Gram: each within the digit-split bound of the oracle, and
+    within the sum of the two bounds of each other, on rows whose magnitudes
+    vary by e^+-3 (so the chunk exponents differ)."""
     torch, gsi = G
     rng = np.random.default_rng(n + p + q)
-    U = _df_dev(torch, gsi, _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-3, 3, (n, 1)))))
-    V = U if sym else _df_dev(torch, gsi, _exact(gsi, rng.standard_normal((n, q))))
+    Uh = _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-3, 3, (n, 1))))
+    Vh = Uh if sym else _exact(gsi, rng.standard_normal((n, q)))
+    U = _df_dev(torch, gsi, Uh)
+    V = U if sym else _df_dev(torch, gsi, Vh)
     outs = []
     for path in (2, 1):
         gsi.set_tensor_path(path)
@@ -189,4 +260,8 @@ def test_oz_gram_tcgen05_equals_mma(G, n, p, q, sym):
         gsi.oz_gram(U, V, Gm, sym=sym)
         outs.append(Gm.cpu().numpy())
     gsi.set_tensor_path(0)
-    assert np.array_equal(outs[0], outs[1])
+    bound = _gram_bound(Uh, Vh)
+    ref = O.gram(Uh, Vh)
+    for o in outs:
+        assert np.all(np.abs(o - ref) <= bound)
+    assert np.all(np.abs(outs[0] - outs[1]) <= 2 * bound)
