@@ -387,7 +387,8 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
 // give identical results.
 // ---------------------------------------------------------------------------
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 512;
+constexpr int TC_WORKERS = 512;                // 16 warps: loads, digits, combination
+constexpr int TC_THREADS = TC_WORKERS + 32;    // + one warp that issues the products
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr int TC_WAIT_LIMIT = 1 << 24;
 
@@ -493,7 +494,8 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   // holds columns 8c + 2j, 8c + 2j + 1 (c < 8); one round of 8 rows per warp
   // (16 warps, 128-row tiles). The next tile's rows are loaded (and the fused
   // left sum formed) while the current tile's products run.
-  static_assert(TC_THREADS / 32 * 8 == TC_M, "one 8-row round per warp");
+  static_assert(TC_WORKERS / 32 * 8 == TC_M, "one 8-row round per worker warp");
+  const bool issuer = warp == TC_WORKERS / 32;
   const int rb = warp * 8, rr = rb + (lane >> 2), j = lane & 3;
   float2 xr[16];
   auto load_tile = [&](int64_t t) {
@@ -527,13 +529,13 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
       xr[2 * c + 1] = x1;
     }
   };
-  load_tile(blockIdx.x);
+  if (!issuer) load_tile(blockIdx.x);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * TC_M;
     // (a) the tile's left operand: row maxima and digits; global reads were
     // 64-byte row segments, and the digit stores hit 32 different banks (row
     // stride 16 B, pair stride 4 B in a core matrix)
-    {
+    if (!issuer) {
       float mx = 0.0f;
 #pragma unroll
       for (int c = 0; c < 16; ++c) mx = fmaxf(mx, fabsf(xr[c].x));
@@ -558,17 +560,26 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // (b) the 28 digit-pair products, grouped by g = i + j
-    if (tid == 0) {
-      for (int g = 0; g < ND; ++g)
-        for (int i = 0; i <= g; ++i)
-          for (int ks = 0; ks < K16 / 16; ++ks)
-            tc_mma(tmem + (uint32_t)(g * NC), tc_desc(abase + i * aplane + ks * 256, K16),
-                   tc_desc(bbase + (g - i) * bplane + ks * 256, K16), idesc, (i > 0 || ks > 0) ? 1u : 0u);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                   : "memory");
+    // (b) the 28 digit-pair products, grouped by g = i + j, issued by the
+    // issuing warp (descriptor start addresses advance in 16-byte units)
+    if (issuer) {
+      if (lane == 0) {
+        const uint64_t da = tc_desc(abase, K16), db = tc_desc(bbase, K16);
+        const uint32_t ap4 = aplane >> 4, bp4 = bplane >> 4;
+#pragma unroll
+        for (int g = 0; g < ND; ++g)
+#pragma unroll
+          for (int i = 0; i <= g; ++i)
+            for (int ks = 0; ks < K16 / 16; ++ks)
+              tc_mma(tmem + (uint32_t)(g * NC), da + i * ap4 + ks * 16, db + (g - i) * bp4 + ks * 16, idesc,
+                     (i > 0 || ks > 0) ? 1u : 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                     : "memory");
+      }
+      __syncwarp();
+    } else {
+      load_tile(tile + gridDim.x);  // registers only: the digit planes are in use
     }
-    load_tile(tile + gridDim.x);  // registers only: the digit planes are in use
     // row-wise epilogue (NC = 64 columns inside the block, even p): warp w
     // owns rows w + 16 k (k < 8), lane l columns 2l, 2l + 1; the first row's
     // elementwise operands are fetched now, each later row's one row ahead
@@ -583,8 +594,8 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
         if (a.dot_with) q2 = *reinterpret_cast<const float4*>(a.dot_with + idx);
       }
     };
-    if (rowwise) fetch_row(0);
-    const bool done = tc_wait(mb, phase);
+    if (rowwise && !issuer) fetch_row(0);
+    const bool done = issuer || tc_wait(mb, phase);
     phase ^= 1u;
     if (__syncthreads_or(!done)) {
       failed = true;
@@ -599,7 +610,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     // on 16 bytes (16-byte stores and loads, four wavefronts per warp access)
     float2* stage = reinterpret_cast<float2*>(Ad);
     const int ss = NC + 2;
-    {
+    if (!issuer) {
       const int row = 32 * (warp & 3) + lane;
       const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
       const int quarter = NC / 4, cbeg = (warp >> 2) * quarter;
@@ -633,6 +644,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     // part 2: row-contiguous pass over the tile: elementwise terms, dots and
     // the store, coalesced
     if (rowwise) {
+      if (!issuer)
 #pragma unroll 1
       for (int k = 0; k < TC_M / 16; ++k) {
         const int rr = warp + 16 * k;

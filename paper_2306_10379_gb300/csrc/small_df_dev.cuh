@@ -62,14 +62,19 @@ static __device__ SdWs sd_carve(unsigned char* base, int p, unsigned char* sbase
   return w;
 }
 
+// Round-robin ordering: in round r (0 <= r < m - 1) slot 0 pairs r with the
+// fixed index m - 1 and slot k pairs (r + k) and (r - k) modulo m - 1; both
+// sums lie in [0, 2 (m - 1)), so one conditional subtraction reduces them.
 static __device__ __forceinline__ void pair_of(int r, int k, int m, int p, int& i, int& j) {
   int a, b;
   if (k == 0) {
     a = r;
     b = m - 1;
   } else {
-    a = (r + k) % (m - 1);
-    b = (r + (m - 1) - k) % (m - 1);
+    a = r + k;
+    if (a >= m - 1) a -= m - 1;
+    b = r + (m - 1) - k;
+    if (b >= m - 1) b -= m - 1;
   }
   i = min(a, b);
   j = max(a, b);
@@ -123,8 +128,8 @@ static __device__ int jacobi_f32(int p, float* A, float* V, SdWs& w, double* red
         w.rj[k] = j;
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
-        int k = e / half, l = e - k * half;
+      // 2 x 2 block (k, l) of J^T A J
+      auto upd_a = [&](int k, int l) {
         int ik = w.ri[k], jk = w.rj[k], il = w.ri[l], jl = w.rj[l];
         float ck = w.rc[k], sk = w.rs[k], cl = w.rc[l], sl = w.rs[l];
         float x00 = A[ik * p + il];
@@ -142,17 +147,33 @@ static __device__ int jacobi_f32(int p, float* A, float* V, SdWs& w, double* red
         if (jl >= 0) A[ik * p + jl] = z01;
         if (jk >= 0) A[jk * p + il] = z10;
         if (jk >= 0 && jl >= 0) A[jk * p + jl] = z11;
-      }
-      // lanes run over rotations (columns), not rows: rows are p apart in
-      // shared memory and would all fall in one bank
-      for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
-        int row = e / half, l = e - row * half;
+      };
+      // columns (il, jl) of row `row` of V by J_l. Lanes run over rotations
+      // (columns), not rows: rows are p apart in shared memory and would all
+      // fall in one bank
+      auto upd_v = [&](int row, int l) {
         int il = w.ri[l], jl = w.rj[l];
-        if (jl < 0) continue;
+        if (jl < 0) return;
         float cl = w.rc[l], sl = w.rs[l];
         float vi = V[row * p + il], vj = V[row * p + jl];
         V[row * p + il] = cl * vi - sl * vj;
         V[row * p + jl] = sl * vi + cl * vj;
+      };
+      if (half <= 32) {  // rotation l <-> lane: no index division
+        const int nw = blockDim.x >> 5, wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+        if (ln < half) {
+          for (int k = wp; k < half; k += nw) upd_a(k, ln);
+          for (int row = wp; row < p; row += nw) upd_v(row, ln);
+        }
+      } else {
+        for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
+          int k = e / half;
+          upd_a(k, e - k * half);
+        }
+        for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
+          int row = e / half;
+          upd_v(row, e - row * half);
+        }
       }
       __syncthreads();
     }
@@ -222,10 +243,9 @@ static __device__ int jacobi_df(int p, float2* A, float2* V, SdWs& w, double* re
         w.rj[k] = j;
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
-        int k = e / half, l = e - k * half;
+      auto upd_a = [&](int k, int l) {
         int ik = w.ri[k], jk = w.rj[k], il = w.ri[l], jl = w.rj[l];
-        if (w.ds[k] == 0.0 && w.ds[l] == 0.0) continue;
+        if (w.ds[k] == 0.0 && w.ds[l] == 0.0) return;
         float2 ck = w.fc[k], sk = w.fs[k];
         float2 cl = w.fc[l], sl = w.fs[l];
         const float2 zero = make_float2(0.f, 0.f);
@@ -246,15 +266,30 @@ static __device__ int jacobi_df(int p, float2* A, float2* V, SdWs& w, double* re
         if (jl >= 0) A[ik * p + jl] = z01;
         if (jk >= 0) A[jk * p + il] = z10;
         if (jk >= 0 && jl >= 0) A[jk * p + jl] = z11;
-      }
-      for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
-        int row = e / half, l = e - row * half;
+      };
+      auto upd_v = [&](int row, int l) {
         int il = w.ri[l], jl = w.rj[l];
-        if (jl < 0 || w.ds[l] == 0.0) continue;
+        if (jl < 0 || w.ds[l] == 0.0) return;
         float2 cl = w.fc[l], sl = w.fs[l];
         float2 vi = V[row * p + il], vj = V[row * p + jl];
         V[row * p + il] = df_add(df_mul(cl, vi), df_neg(df_mul(sl, vj)));
         V[row * p + jl] = df_add(df_mul(sl, vi), df_mul(cl, vj));
+      };
+      if (half <= 32) {  // rotation l <-> lane: no index division
+        const int nw = blockDim.x >> 5, wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+        if (ln < half) {
+          for (int k = wp; k < half; k += nw) upd_a(k, ln);
+          for (int row = wp; row < p; row += nw) upd_v(row, ln);
+        }
+      } else {
+        for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
+          int k = e / half;
+          upd_a(k, e - k * half);
+        }
+        for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
+          int row = e / half;
+          upd_v(row, e - row * half);
+        }
       }
       __syncthreads();
     }
