@@ -242,19 +242,23 @@ gsi_status df_combine3(int64_t count, float2 a, const float2* W, float2 b, const
   return GSI_OK;
 }
 
-__global__ void df_sum_parts_kernel(int nparts, const float2* parts, double* out) {
+__global__ void df_sum_parts_kernel(int nparts, const float2* parts, double* out, const float* rinf) {
   if (threadIdx.x != 0) return;
   float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
+  float m = 0.f;
   for (int b = 0; b < nparts; ++b) {
     t0 = df_add(t0, parts[2 * b]);
     t1 = df_add(t1, parts[2 * b + 1]);
+    if (rinf) m = fmaxf(m, rinf[b]);
   }
   out[0] = df_to_double(t0);
   out[1] = df_to_double(t1);
+  if (rinf) out[2] = (double)m;
 }
 
-gsi_status df_sum_parts(int nparts, const float2* parts, double* out, cudaStream_t st) {
-  df_sum_parts_kernel<<<1, 32, 0, st>>>(nparts, parts, out);
+gsi_status df_sum_parts(int nparts, const float2* parts, double* out, cudaStream_t st,
+                        const float* rinf_parts) {
+  df_sum_parts_kernel<<<1, 32, 0, st>>>(nparts, parts, out, rinf_parts);
   GSI_LAUNCH_CHECK();
   return GSI_OK;
 }

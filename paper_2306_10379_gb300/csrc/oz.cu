@@ -11,11 +11,13 @@
 // column and row chunk (gram: 64 rows in the mma.sync kernel, 256 or 128 in
 // the tcgen05 kernel):
 //   x = 2^(E-7) * sum_{i<7} d_i 2^(-7 i)   (truncation below 2^(E-49)).
-// Digits are exact in bf16, products of two digits are exact in fp32, and the
-// 28 digit pairs (i + i' <= 6) are summed per "group" g = i + i' in fp32
-// accumulators whose partial sums stay below 2^24 for contraction lengths up
-// to 256, so the tensor-core accumulation is exact. The 7 group sums are then
-// combined in df64: OUT = 2^(E_r + F_j - 14) sum_g S_g 2^(-7 g).
+// Digits are exact in bf16 and are stored with their weights, d_i 2^(-7 i);
+// products of two digits are exact in fp32, and the 28 digit pairs
+// (i + i' <= 6) are summed per "group" g = i + i' in fp32 accumulators whose
+// partial sums stay below 2^24 times the group's weight 2^(-7 g) for
+// contraction lengths up to 256, so the tensor-core accumulation is exact.
+// The 7 group sums S_g are then combined in df64:
+// OUT = 2^(E_r + F_j - 14) sum_g S_g.
 #include <cuda_bf16.h>
 #include <stdlib.h>
 #include <string.h>
@@ -49,23 +51,27 @@ __device__ __forceinline__ int exponent_above(float maxabs) {
   return max(e + 1, -100);
 }
 
-// The 7 digits of (h + l) on the grid of 2^(E-7): digits 0..2 come from h
+// The 7 digits of (h + l) on the grid of 2^(E-7), each returned with its
+// weight: d[i] = d_i 2^(-7 i) (exact in bf16 like d_i itself, so a product of
+// digits i and j already carries the 2^(-7 (i + j)) of its group). In the
+// frame a = (h + l) 2^(7-E), |a| < 128: adding 1.5 * 2^(23 - 7i) rounds a to
+// a multiple of 2^(-7i), and a <- a - d[i] is exact. Digits 0..2 come from h
 // alone, then l is folded in (at that point h's remainder is a multiple of
-// 2^4 in the digit frame and |l| <= 8, so one rounding of at most 2^-45 of
-// the scale can occur), digits 3..6 follow. Each step is exact:
-// d = rint(a), a <- 128 (a - d).
+// 2^-17 and |l 2^(7-E)| <= 2^-17 * 8, so one rounding of at most 2^-45 of the
+// scale can occur), digits 3..6 follow.
 template <int N>
 __device__ __forceinline__ void digitsN(float h, float l, int E, float d[N]) {
   const float s = exp2i(7 - E);
   float a = __fmul_rn(h, s);
-  float b = __fmul_rn(__fmul_rn(l, s), 2097152.0f);
+  const float b = __fmul_rn(l, s);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     if (i == 3) a = __fadd_rn(a, b);
-    float t = __fadd_rn(a, MAGIC);
-    float di = __fsub_rn(t, MAGIC);
+    const float m = MAGIC * exp2i(-7 * i);  // exact power of two, constant per i
+    float t = __fadd_rn(a, m);
+    float di = __fsub_rn(t, m);
     d[i] = di;
-    a = __fmul_rn(__fsub_rn(a, di), 128.0f);
+    a = __fsub_rn(a, di);
   }
 }
 
@@ -74,15 +80,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// sum_g S_g 2^(-7 g) as df64 (Horner from the smallest group, TwoSum per step)
+// sum_g S_g as df64, where S_g is the group sum of weighted digit products
+// (an integer times 2^(-7 g)): from the smallest group up, TwoSum per step
 template <int N>
 __device__ __forceinline__ float2 combine_groups(const float S[N]) {
   float h = S[N - 1], l = 0.0f;
 #pragma unroll
   for (int g = N - 2; g >= 0; --g) {
-    float hs = __fmul_rn(h, 0.0078125f);
-    l = __fmul_rn(l, 0.0078125f);
-    float2 t = two_sum(S[g], hs);
+    float2 t = two_sum(S[g], h);
     h = t.x;
     l = __fadd_rn(l, t.y);
   }
@@ -487,6 +492,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
                          ((uint32_t)(TC_M >> 4) << 24);
   const uint32_t abase = smem_addr(Ad), bbase = smem_addr(Bd), mb = smem_addr(mbar);
   float2 dacc0 = make_float2(0.f, 0.f), dacc1 = make_float2(0.f, 0.f);
+  float rmax = 0.f;  // largest row sum of |hi(out)| seen by this warp
   uint32_t phase = 0;
   bool failed = false;
   const int64_t ntiles = (n + TC_M - 1) / TC_M;
@@ -507,7 +513,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
       float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
       if (live && k < p) {
         const int64_t o = R * p + k;
-        if (k + 1 < p && (o & 1) == 0) {  // 16-byte aligned pair
+        if (a.vec16 && k + 1 < p && (o & 1) == 0) {  // 16-byte aligned pair
           const float4 v = *reinterpret_cast<const float4*>(a.U[0] + o);
           x0 = make_float2(v.x, v.y);
           x1 = make_float2(v.z, v.w);
@@ -580,14 +586,16 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     } else {
       load_tile(tile + gridDim.x);  // registers only: the digit planes are in use
     }
-    // row-wise epilogue (NC = 64 columns inside the block, even p): warp w
-    // owns rows w + 16 k (k < 8), lane l columns 2l, 2l + 1; the first row's
-    // elementwise operands are fetched now, each later row's one row ahead
-    const bool rowwise = NC == 64 && col0 + 64 <= p && (p & 1) == 0;
+    // row-wise epilogue (all p <= 64 columns in this block, p even, aligned
+    // blocks): warp w owns rows w + 16 k (k < 8), lane l columns 2l, 2l + 1
+    // (lanes with 2l >= p idle); the first row's elementwise operands are
+    // fetched now, each later row's one row ahead
+    const bool rowwise = a.vec16 && col0 == 0 && p <= 64 && (p & 1) == 0;
+    const bool lact = 2 * lane < p;
     float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0;
     auto fetch_row = [&](int k) {
       const int64_t R = r0 + warp + 16 * k;
-      if (R < n) {
+      if (R < n && lact) {
         const int64_t idx = R * p + col0 + 2 * lane;
         if (a.ne > 0) q0 = *reinterpret_cast<const float4*>(a.E[0] + idx);
         if (a.ne > 1) q1 = *reinterpret_cast<const float4*>(a.E[1] + idx);
@@ -652,8 +660,12 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
         const float4 e0 = q0, e1 = q1, w2 = q2;
         if (k + 1 < TC_M / 16) fetch_row(k + 1);
         if (R >= n) continue;
-        const float4 sv = *reinterpret_cast<const float4*>(stage + rr * ss + 2 * lane);
-        float2 y0 = make_float2(sv.x, sv.y), y1 = make_float2(sv.z, sv.w);
+        float2 y0 = make_float2(0.f, 0.f), y1 = y0;
+        if (lact) {
+          const float4 sv = *reinterpret_cast<const float4*>(stage + rr * ss + 2 * lane);
+          y0 = make_float2(sv.x, sv.y);
+          y1 = make_float2(sv.z, sv.w);
+        }
         if (a.ne > 0) {
           y0 = df_add(y0, df_mul(a.ce[0], make_float2(e0.x, e0.y)));
           y1 = df_add(y1, df_mul(a.ce[0], make_float2(e0.z, e0.w)));
@@ -670,7 +682,13 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
           dacc1 = df_add(dacc1, df_mul(y0, make_float2(w2.x, w2.y)));
           dacc1 = df_add(dacc1, df_mul(y1, make_float2(w2.z, w2.w)));
         }
-        *reinterpret_cast<float4*>(a.out + R * p + col0 + 2 * lane) = make_float4(y0.x, y0.y, y1.x, y1.y);
+        if (lact) *reinterpret_cast<float4*>(a.out + R * p + 2 * lane) = make_float4(y0.x, y0.y, y1.x, y1.y);
+        if (a.rinf_part) {  // this row's sum_j |hi(out[r, j])|, the same in every lane
+          float rs = fabsf(y0.x) + fabsf(y1.x);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+          rmax = fmaxf(rmax, rs);
+        }
       }
     } else
     for (int e = tid; e < TC_M * NC; e += TC_THREADS) {
@@ -729,6 +747,16 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
       const int b = blockIdx.y * gridDim.x + blockIdx.x;
       a.dot_part[2 * b] = s0;
       a.dot_part[2 * b + 1] = s1;
+    }
+  }
+  if (a.rinf_part) {
+    __shared__ float redm[TC_THREADS / 32];
+    if (lane == 0) redm[warp] = rmax;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.f;
+      for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, redm[w]);
+      a.rinf_part[blockIdx.y * gridDim.x + blockIdx.x] = m;
     }
   }
 }
@@ -1141,9 +1169,10 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
           float S[ND];
 #pragma unroll
           for (int h = 0; h < ND; ++h) S[h] = __uint_as_float(v[h][e]);
-          // top: sum_h S_h 2^(-7h); bottom: 2^-7 sum_{h<6} S_h 2^(-7h)
+          // top: groups 0..6 (even digits of U); bottom: groups 1..6 (odd
+          // digits), block h holding group h + 1, each sum carrying its weight
           const float2 w = top ? combine_groups<ND>(S) : combine_groups<ND - 1>(S);
-          const int sc = Eu[arow] + Evv[cb + c0 + e] - 14 - (top ? 0 : 7);
+          const int sc = Eu[arow] + Evv[cb + c0 + e] - 14;
           const float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
           res[c0 + e] = df_add(res[c0 + e], make_float2(w.x * f1 * f2, w.y * f1 * f2));
         }
@@ -1225,7 +1254,9 @@ size_t oz_rhs_bytes(int p, int nk) {
 gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const double* const M[2],
                    const double s[2], int ne, const float2* const E[2], const float2 ce[2],
                    float2* out, float2* dot_part, const float2* dot_with, bool dot_self,
-                   void* rhs_ws, cudaStream_t st, int* nparts, int nd) {
+                   void* rhs_ws, cudaStream_t st, int* nparts, int nd, float* rinf_part,
+                   bool* rinf_done) {
+  if (rinf_done) *rinf_done = false;
   if (nk < 1 || nk > 2 || ne < 0 || ne > 2 || p < 1 || p > 128 || (nd != 3 && nd != ND))
     return GSI_ERR_ARG;
   bool fuse = nk == 2 && M[1] == M[0] && s[0] != 0.0;
@@ -1243,7 +1274,7 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
     const float2* E1[2] = {out, out};
     float2 c1[2] = {make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
     return oz_gemm(n, p, 1, U1, M1, s1, 1, E1, c1, out, dot_part, dot_with, dot_self, rhs_ws, st,
-                   nparts, nd);
+                   nparts, nd, rinf_part, rinf_done);
   }
   const int p16 = pad16(p), K16 = p16;
   const int ncs = (p16 + 63) / 64;
@@ -1271,6 +1302,12 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   a.dot_part = dot_part;
   a.dot_with = dot_with;
   a.dot_self = dot_self ? 1 : 0;
+  {
+    const void* ptrs[6] = {a.U[0], a.U[1], ne > 0 ? E[0] : nullptr, ne > 1 ? E[1] : nullptr, dot_with, out};
+    a.vec16 = 1;
+    for (const void* q : ptrs)
+      if (((uintptr_t)q & 15) != 0) a.vec16 = 0;
+  }
   const int NCmax = std::min(64, p16);
   if (nd == ND && K16 <= 64 && tensor_path() != 1) {
     const size_t tsm = oz_gemm_tc_smem(K16, NCmax);
@@ -1278,6 +1315,11 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
     int gx = (int)std::min<int64_t>((n + TC_M - 1) / TC_M, (int64_t)sm_count());
     gx = std::max(gx, 1);
     if (nparts) *nparts = gx * ncs;
+    // the row sums are formed where one warp holds whole rows (the kernel's
+    // row-wise epilogue: one column block, even p, aligned blocks)
+    const bool rows = rinf_part && a.vec16 && ncs == 1 && (p & 1) == 0;
+    a.rinf_part = rows ? rinf_part : nullptr;
+    if (rinf_done) *rinf_done = rows;
     oz_gemm_tc_kernel<<<dim3(gx, ncs), TC_THREADS, tsm, st>>>(n, p, p16, K16, a);
     GSI_LAUNCH_CHECK();
     return GSI_OK;

@@ -20,6 +20,8 @@ struct OzGemmArgs {
   float2* dot_part;          // per-block partials {<out,out>, <out,dot_with>} or null
   const float2* dot_with;
   int dot_self;
+  int vec16;                 // every block pointer 16-byte aligned: 16-byte loads and stores
+  float* rinf_part;          // per-block max_r sum_j |hi(out[r,j])| (row-wise epilogue only) or null
 };
 
 int pad16(int x);
@@ -32,10 +34,14 @@ size_t oz_rhs_bytes(int p, int nk);
 // df64 on the fly (one product of contraction length p).
 // rhs_ws: oz_rhs_bytes(p, nk) bytes of device scratch for the right operand's digits.
 // dot_part (optional): 2 * (*nparts) df64 partial sums.
+// rinf_part (optional, oz_gemm_max_parts(p) floats): per-block maxima of the
+// row sums sum_j |out[r, j]| (float32 sums of the high words), formed in the
+// tcgen05 kernel's row-wise epilogue; *rinf_done tells whether they were.
 gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const double* const M[2],
                    const double s[2], int ne, const float2* const E[2], const float2 ce[2],
                    float2* out, float2* dot_part, const float2* dot_with, bool dot_self,
-                   void* rhs_ws, cudaStream_t st, int* nparts, int nd = 7);
+                   void* rhs_ws, cudaStream_t st, int* nparts, int nd = 7,
+                   float* rinf_part = nullptr, bool* rinf_done = nullptr);
 int oz_gemm_max_parts(int p);
 size_t oz_gram_scratch_bytes(int64_t n, int p, int q, bool sym);
 // G = U^T V (float64 p x q); sym: U == V, only the upper half is computed.
@@ -64,7 +70,9 @@ gsi_status df_axpby(int64_t count, float2 a, const float2* x, float2 b, float2* 
 // out = a W + b Z + e Zp elementwise (df64 scalars; Zp may be null)
 gsi_status df_combine3(int64_t count, float2 a, const float2* W, float2 b, const float2* Z, float2 e,
                        const float2* Zp, float2* out, cudaStream_t st);
-// sum of df64 partial pairs into out[0..1] (float64)
-gsi_status df_sum_parts(int nparts, const float2* parts, double* out, cudaStream_t st);
+// sum of df64 partial pairs into out[0..1] (float64); with rinf_parts, also
+// out[2] = max of rinf_parts[0..nparts)
+gsi_status df_sum_parts(int nparts, const float2* parts, double* out, cudaStream_t st,
+                        const float* rinf_parts = nullptr);
 
 }  // namespace gsi

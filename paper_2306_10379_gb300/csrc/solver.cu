@@ -125,6 +125,8 @@ struct gsi_ctx {
   float2* oz_gram_ws = nullptr;
   void* oz_rhs_ws = nullptr;
   float2* oz_parts = nullptr;
+  float* oz_rinf = nullptr;  // per-block row-norm maxima of a fused residual product
+  bool rinf_fused = false;   // the last block product also left max_r sum_j |R[r,j]| in dout[2]
   double* dots_ws = nullptr;
   double* small_ws = nullptr;
   double* host = nullptr;  // pinned readback buffer
@@ -263,13 +265,16 @@ gsi_status op_gram(gsi_ctx* c, const void* U, const void* V, bool sym, double* G
 
 // out = s0 U0 M0 (+ s1 U1 M1) + c0 E0 (+ c1 E1); optional dots (emu: fused;
 // f64: separate pass) <out,out> -> dout[0], <out,dw> -> dout[1].
+// row_inf: also max_r sum_j |out[r, j]| -> dout[2] where the product can form
+// it (sets c->rinf_fused).
 gsi_status op_blockmul(gsi_ctx* c, int nk, const void* U0, const double* M0, double s0,
                        const void* U1, const double* M1, double s1, int ne, const void* E0,
                        double c0, const void* E1, double c1, void* outp, bool dot_self,
-                       const void* dw) {
+                       const void* dw, bool row_inf = false) {
   prof_begin(c);
   gsi_status s;
   const bool want = dot_self || dw;
+  c->rinf_fused = false;
   if (c->emu) {
     const float2* U[2] = {(const float2*)U0, (const float2*)(U1 ? U1 : U0)};
     const double* M[2] = {M0, M1 ? M1 : M0};
@@ -277,9 +282,12 @@ gsi_status op_blockmul(gsi_ctx* c, int nk, const void* U0, const double* M0, dou
     const float2* E[2] = {(const float2*)E0, (const float2*)E1};
     float2 ce[2] = {df_from_double(c0), df_from_double(c1)};
     int np = 0;
+    bool fused = false;
     s = oz_gemm(c->n, c->p, nk, U, M, sc, ne, E, ce, (float2*)outp, want ? c->oz_parts : nullptr,
-                (const float2*)dw, dot_self, c->oz_rhs_ws, c->st, &np);
-    if (s == GSI_OK && want) s = df_sum_parts(np, c->oz_parts, c->dout, c->st);
+                (const float2*)dw, dot_self, c->oz_rhs_ws, c->st, &np, 7,
+                want && row_inf ? c->oz_rinf : nullptr, &fused);
+    if (s == GSI_OK && want) s = df_sum_parts(np, c->oz_parts, c->dout, c->st, fused ? c->oz_rinf : nullptr);
+    c->rinf_fused = s == GSI_OK && fused;
   } else {
     RowMulArgs a{};
     a.nk = nk;
@@ -349,15 +357,21 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
   for (;;) {
     GSI_TRY(op_gram(c, c->X, c->Y, true, c->Cm));  // C = X^T A X, symmetric
     const bool want_rp = cg && c->have_prev;
-    // R = Y - X C with <R,R> and <R,R_prev>
+    // R = Y - X C with <R,R>, <R,R_prev> and (where the product forms it)
+    // max_r sum_j |R[r,j]|
     GSI_TRY(op_blockmul(c, 1, c->X, c->Cm, -1.0, nullptr, nullptr, 0.0, 1, c->Y, 1.0, nullptr, 0.0,
-                        c->R, true, want_rp ? c->Rp : nullptr));
-    GSI_TRY(readback(c, c->dout, 2));
+                        c->R, true, want_rp ? c->Rp : nullptr, true));
+    const bool rinf_fused = c->rinf_fused;
+    GSI_TRY(readback(c, c->dout, rinf_fused ? 3 : 2));
     rr = c->host[0];
     rp = want_rp ? c->host[1] : 0.0;
-    GSI_TRY(op_rowinf(c, c->R));
-    GSI_TRY(readback(c, c->dout + 2, 1));
-    rinf = c->host[0];
+    if (rinf_fused) {
+      rinf = c->host[2];
+    } else {
+      GSI_TRY(op_rowinf(c, c->R));
+      GSI_TRY(readback(c, c->dout + 2, 1));
+      rinf = c->host[0];
+    }
     if (!isfinite(rr)) return GSI_ERR_NONFINITE;
     if (c->res0_inf < 0.0) c->res0_inf = rinf;
     c->rel = sqrt(rr) / c->anorm;
@@ -782,6 +796,7 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       CK(dev_alloc(c, (void**)&c->oz_gram_ws, oz_gram_scratch_bytes(n, p, p, false)));
       CK(dev_alloc(c, &c->oz_rhs_ws, oz_rhs_bytes(p, 2)));
       CK(dev_alloc(c, (void**)&c->oz_parts, (size_t)oz_gemm_max_parts(p) * 2 * sizeof(float2)));
+      CK(dev_alloc(c, (void**)&c->oz_rinf, (size_t)oz_gemm_max_parts(p) * sizeof(float)));
       CK(dev_alloc(c, (void**)&c->dots_ws, (size_t)df_dots_blocks(n * p) * 3 * sizeof(float2)));
     } else {
       CK(dev_alloc(c, (void**)&c->gram_ws, gram_scratch_doubles(n, p, p) * sizeof(double)));

@@ -331,3 +331,30 @@ def test_reset_and_profile(torch_cuda):
     assert i1["iters"] == i2["iters"] and i1["rel_residual"] == i2["rel_residual"]
     assert prof["spmm"]["launches"] == i2["matvecs"]  # includes the start-block matvec of reset
     assert all(prof[k]["ms"] > 0 for k in ("spmm", "gram", "blockmul", "small"))
+
+
+def test_fused_row_norm_matches_separate_pass(torch_cuda):
+    """max_r sum_j |R[r, j]| formed in the tcgen05 block product's row-wise
+    epilogue (tensor path 0, p even <= 64) against the separate reduction
+    kernel (mma.sync path 1, where the product does not form it). The two
+    paths' Grams round differently (256/128- against 64-row exponent
+    chunks), so the runs agree to rounding: same iteration count, residuals
+    within 1e-4 relative, infinity-norm residuals within 1e-3 (a lost row or a
+    wrong reduction would be off by far more)."""
+    from paper_2306_10379_gb300 import gsi
+    dims, p = (30, 28), 8
+    A = I.fd_laplacian(dims)
+    lam = I.laplacian_eigenvalues(dims)
+    out = []
+    for path in (0, 1):
+        gsi.set_tensor_path(path)
+        try:
+            with gsi.Solver(A, p, I.start_block(A.n, p, 5), method="cg", tol=1e-8, anorm=lam[0]) as s:
+                out.append(s.solve())
+        finally:
+            gsi.set_tensor_path(0)
+    a, b = out
+    assert a["iters"] == b["iters"]
+    assert abs(a["rel_residual"] - b["rel_residual"]) <= 1e-4 * b["rel_residual"]
+    assert np.isfinite(a["rel_residual_inf"]) and a["rel_residual_inf"] > 0
+    assert abs(a["rel_residual_inf"] - b["rel_residual_inf"]) <= 1e-3 * b["rel_residual_inf"]
