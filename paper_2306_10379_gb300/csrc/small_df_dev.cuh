@@ -307,26 +307,56 @@ static __device__ __forceinline__ void mac_df(float& sh, float& se, float2 a, fl
   se = __fadd_rn(se, __fadd_rn(t.y, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, pe))));
 }
 
-// Out = op(X) Y, op = transpose if tx; df64 p x p, block-parallel.
-static __device__ void mm_df(int p, const float2* X, bool tx, const float2* Y, float2* Out) {
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    int i = e / p, j = e - i * p;
-    float sh = 0.f, se = 0.f;
-    for (int k = 0; k < p; ++k) mac_df(sh, se, tx ? X[k * p + i] : X[i * p + k], Y[k * p + j]);
-    Out[e] = fast_two_sum(sh, se);
+// Out = op(X) Y, op = transpose if tx; df64 p x p, block-parallel; the
+// result goes to Out (df64) or, with Out null, to Outd (float64). For
+// p <= 64 a thread forms the 2 x 2 outputs (i, i + 1) x (j, j + 32), i from
+// its warp, j its lane: the row operand is a warp broadcast and each loaded
+// value serves two products, which halves the shared-memory loads of the
+// one-output-per-thread form. Every output sums over k in the same order
+// either way.
+static __device__ void mm_df_to(int p, const float2* X, bool tx, const float2* Y, float2* Out, double* Outd) {
+  auto put = [&](int e, float sh, float se) {
+    const float2 v = fast_two_sum(sh, se);
+    if (Out) Out[e] = v;
+    else Outd[e] = df_to_double(v);
+  };
+  if (p <= 64) {
+    const int nw = blockDim.x >> 5, wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    const int j0 = ln, j1 = ln + 32;
+    const bool c0 = j0 < p, c1 = j1 < p;
+    const int sx = tx ? p : 1;
+    const float2 zero = make_float2(0.f, 0.f);
+    for (int i = 2 * wp; i < p; i += 2 * nw) {
+      const bool r1 = i + 1 < p;
+      const float2* x0p = X + (tx ? i : i * p);
+      const float2* x1p = X + (tx ? i + 1 : (i + 1) * p);
+      float h00 = 0.f, e00 = 0.f, h01 = 0.f, e01 = 0.f, h10 = 0.f, e10 = 0.f, h11 = 0.f, e11 = 0.f;
+      for (int k = 0; k < p; ++k) {
+        const float2 x0 = x0p[k * sx], x1 = r1 ? x1p[k * sx] : zero;
+        const float2 y0 = c0 ? Y[k * p + j0] : zero, y1 = c1 ? Y[k * p + j1] : zero;
+        mac_df(h00, e00, x0, y0);
+        mac_df(h01, e01, x0, y1);
+        mac_df(h10, e10, x1, y0);
+        mac_df(h11, e11, x1, y1);
+      }
+      if (c0) put(i * p + j0, h00, e00);
+      if (c1) put(i * p + j1, h01, e01);
+      if (r1 && c0) put((i + 1) * p + j0, h10, e10);
+      if (r1 && c1) put((i + 1) * p + j1, h11, e11);
+    }
+  } else {
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+      int i = e / p, j = e - i * p;
+      float sh = 0.f, se = 0.f;
+      for (int k = 0; k < p; ++k) mac_df(sh, se, tx ? X[k * p + i] : X[i * p + k], Y[k * p + j]);
+      put(e, sh, se);
+    }
   }
   __syncthreads();
 }
 
-// Out = X op(Y)^T variant: Out = X Y^T
-static __device__ void mm_df_nt(int p, const float2* X, const float2* Y, float2* Out) {
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    int i = e / p, j = e - i * p;
-    float sh = 0.f, se = 0.f;
-    for (int k = 0; k < p; ++k) mac_df(sh, se, X[i * p + k], Y[j * p + k]);
-    Out[e] = fast_two_sum(sh, se);
-  }
-  __syncthreads();
+static __device__ void mm_df(int p, const float2* X, bool tx, const float2* Y, float2* Out) {
+  mm_df_to(p, X, tx, Y, Out, nullptr);
 }
 
 // Out = G V with G float64 (symmetrised), V df64; G is converted once into Gd.
@@ -431,13 +461,13 @@ static __device__ int inv_sqrt_in_basis(int p, SdWs& w, double* M, int* flag) {
   }
   __syncthreads();
   mm_df(p, w.Vd, false, w.Ud, w.Td);  // T = V N
+  // M = T V^T: V^T into the free Ud, then a plain product into M (float64)
   for (int e = threadIdx.x; e < q; e += blockDim.x) {
     int i = e / p, j = e - i * p;
-    float sh = 0.f, se = 0.f;
-    for (int k = 0; k < p; ++k) mac_df(sh, se, w.Td[i * p + k], w.Vd[j * p + k]);
-    M[e] = df_to_double(fast_two_sum(sh, se));
+    w.Ud[j * p + i] = w.Vd[e];
   }
   __syncthreads();
+  mm_df_to(p, w.Td, false, w.Ud, nullptr, M);
   return *flag;
 }
 
