@@ -227,11 +227,15 @@ __device__ inline double brent_warp(double a, double b, double fa, double fb, in
 // xi_min (capped at xi_max) until phi' >= 0, then Brent.
 __device__ inline double get_mu_warp(int p, const double* al, const double* be, const double* ga,
                          const double* ze, int* ev) {
-  double sb = 0.0;
-  for (int i = 0; i < p; ++i) sb += be[i];  // same order in every lane
+  double sb = 0.0;  // summed in index order by lane 0, then broadcast
+  if ((threadIdx.x & 31) == 0)
+    for (int i = 0; i < p; ++i) sb += be[i];
+  sb = __shfl_sync(0xffffffffu, sb, 0);
+  // the xi_i over the lanes (lane j takes j, j + 32, ...); min, max and
+  // count are exact, so every lane ends with the same values
   double xmin = INFINITY, xmax = -INFINITY;
   int cnt = 0;
-  for (int i = 0; i < p; ++i) {
+  for (int i = threadIdx.x & 31; i < p; i += 32) {
     double b = be[i], z = ze[i];
     if (!(b > ALG3_EPS * sb) || !(z > 0.0)) continue;
     double d = ga[i] - al[i] * b;
@@ -240,6 +244,11 @@ __device__ inline double get_mu_warp(int p, const double* al, const double* be, 
     xmin = fmin(xmin, xi);
     xmax = fmax(xmax, xi);
     ++cnt;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    xmin = fmin(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+    xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   }
   *ev = 0;
   if (cnt == 0) return 0.0;

@@ -81,21 +81,33 @@ static __device__ __forceinline__ void pair_of(int r, int k, int m, int p, int& 
   if (j >= p) j = -1;  // paired with the dummy index of an odd p: identity on i
 }
 
+// The warps' partial sums are added in warp order by one thread and the
+// total broadcast: one float64 add per warp instead of one per thread and
+// warp on the slow float64 pipe.
 static __device__ double block_sum(double v, double* red) {
+  __shared__ double total;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    total = s;
+  }
   __syncthreads();
-  return s;
+  return total;
 }
 
 // float32 Jacobi on Af (p x p), rotations accumulated into Vf.
 static __device__ int jacobi_f32(int p, float* A, float* V, SdWs& w, double* red, int max_sweeps,
                           double rel_tol) {
   const int m = (p + 1) & ~1, half = m / 2;
+  // rotation tables held in registers for the whole call
+  float* const rc = w.rc;
+  float* const rs = w.rs;
+  int* const ri = w.ri;
+  int* const rj = w.rj;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
@@ -122,16 +134,16 @@ static __device__ int jacobi_f32(int p, float* A, float* V, SdWs& w, double* red
             s = t * c;
           }
         }
-        w.rc[k] = c;
-        w.rs[k] = s;
-        w.ri[k] = i;
-        w.rj[k] = j;
+        rc[k] = c;
+        rs[k] = s;
+        ri[k] = i;
+        rj[k] = j;
       }
       __syncthreads();
       // 2 x 2 block (k, l) of J^T A J
       auto upd_a = [&](int k, int l) {
-        int ik = w.ri[k], jk = w.rj[k], il = w.ri[l], jl = w.rj[l];
-        float ck = w.rc[k], sk = w.rs[k], cl = w.rc[l], sl = w.rs[l];
+        int ik = ri[k], jk = rj[k], il = ri[l], jl = rj[l];
+        float ck = rc[k], sk = rs[k], cl = rc[l], sl = rs[l];
         float x00 = A[ik * p + il];
         float x01 = jl >= 0 ? A[ik * p + jl] : 0.f;
         float x10 = jk >= 0 ? A[jk * p + il] : 0.f;
@@ -152,9 +164,9 @@ static __device__ int jacobi_f32(int p, float* A, float* V, SdWs& w, double* red
       // (columns), not rows: rows are p apart in shared memory and would all
       // fall in one bank
       auto upd_v = [&](int row, int l) {
-        int il = w.ri[l], jl = w.rj[l];
+        int il = ri[l], jl = rj[l];
         if (jl < 0) return;
-        float cl = w.rc[l], sl = w.rs[l];
+        float cl = rc[l], sl = rs[l];
         float vi = V[row * p + il], vj = V[row * p + jl];
         V[row * p + il] = cl * vi - sl * vj;
         V[row * p + jl] = sl * vi + cl * vj;
@@ -201,6 +213,12 @@ static __device__ __forceinline__ float2 df_rsqrt(float2 q) {
 // float64) accumulated into Vd.
 static __device__ int jacobi_df(int p, float2* A, float2* V, SdWs& w, double* red, int max_sweeps) {
   const int m = (p + 1) & ~1, half = m / 2;
+  // rotation tables held in registers for the whole call
+  float2* const fc = w.fc;
+  float2* const fs = w.fs;
+  double* const ds = w.ds;
+  int* const ri = w.ri;
+  int* const rj = w.rj;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
@@ -236,18 +254,18 @@ static __device__ int jacobi_df(int p, float2* A, float2* V, SdWs& w, double* re
             act = true;
           }
         }
-        w.fc[k] = c;
-        w.fs[k] = s;
-        w.ds[k] = act ? 1.0 : 0.0;
-        w.ri[k] = i;
-        w.rj[k] = j;
+        fc[k] = c;
+        fs[k] = s;
+        ds[k] = act ? 1.0 : 0.0;
+        ri[k] = i;
+        rj[k] = j;
       }
       __syncthreads();
       auto upd_a = [&](int k, int l) {
-        int ik = w.ri[k], jk = w.rj[k], il = w.ri[l], jl = w.rj[l];
-        if (w.ds[k] == 0.0 && w.ds[l] == 0.0) return;
-        float2 ck = w.fc[k], sk = w.fs[k];
-        float2 cl = w.fc[l], sl = w.fs[l];
+        int ik = ri[k], jk = rj[k], il = ri[l], jl = rj[l];
+        if (ds[k] == 0.0 && ds[l] == 0.0) return;
+        float2 ck = fc[k], sk = fs[k];
+        float2 cl = fc[l], sl = fs[l];
         const float2 zero = make_float2(0.f, 0.f);
         float2 x00 = A[ik * p + il];
         float2 x01 = jl >= 0 ? A[ik * p + jl] : zero;
@@ -268,9 +286,9 @@ static __device__ int jacobi_df(int p, float2* A, float2* V, SdWs& w, double* re
         if (jk >= 0 && jl >= 0) A[jk * p + jl] = z11;
       };
       auto upd_v = [&](int row, int l) {
-        int il = w.ri[l], jl = w.rj[l];
-        if (jl < 0 || w.ds[l] == 0.0) return;
-        float2 cl = w.fc[l], sl = w.fs[l];
+        int il = ri[l], jl = rj[l];
+        if (jl < 0 || ds[l] == 0.0) return;
+        float2 cl = fc[l], sl = fs[l];
         float2 vi = V[row * p + il], vj = V[row * p + jl];
         V[row * p + il] = df_add(df_mul(cl, vi), df_neg(df_mul(sl, vj)));
         V[row * p + jl] = df_add(df_mul(sl, vi), df_mul(cl, vj));
