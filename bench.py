@@ -36,10 +36,11 @@ WARMUP_ITERS = 200
 # to the bench size by the rows processed (traffic grows in proportion).
 NCU_TRAFFIC = {
     # DRAM read + write per launch at n = 512,000, p = 64 (profiles/digit_kernels_fd3d80_p64.md),
-    # averaged over one iteration's launches of the class
-    "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.2e6 + 3.8e6) + 3 * (524.5e6 + 3.6e6)) / 5},
-    "blockmul": {"n": 512000, "p": 64, "bytes": ((787.8e6 + 248.4e6) + (787.3e6 + 246.8e6)
-                                                  + 2 * (524.5e6 + 233.3e6)) / 4},
+    # averaged over one iteration's launches of the class (2 U^T U + 3 U^T V Grams; 2 fused
+    # retractions + 2 products with elementwise terms, R's counters standing for D's)
+    "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.249e6 + 3.685e6) + 3 * (524.391e6 + 3.592e6)) / 5},
+    "blockmul": {"n": 512000, "p": 64, "bytes": ((524.523e6 + 226.326e6) + (524.506e6 + 226.865e6)
+                                                  + 2 * (786.842e6 + 240.490e6)) / 4},
     "spmm": {"n": 512000, "p": 64, "bytes": 308.8e6 + 229.4e6},
 }
 

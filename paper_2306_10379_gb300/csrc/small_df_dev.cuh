@@ -216,7 +216,7 @@ static __device__ int jacobi_df(int p, float2* A, float2* V, SdWs& w, double* re
   // rotation tables held in registers for the whole call
   float2* const fc = w.fc;
   float2* const fs = w.fs;
-  double* const ds = w.ds;
+  int* const act_k = reinterpret_cast<int*>(w.ds);  // rotation k active (1) or identity (0)
   int* const ri = w.ri;
   int* const rj = w.rj;
   int sweep = 0;
@@ -256,14 +256,14 @@ static __device__ int jacobi_df(int p, float2* A, float2* V, SdWs& w, double* re
         }
         fc[k] = c;
         fs[k] = s;
-        ds[k] = act ? 1.0 : 0.0;
+        act_k[k] = act ? 1 : 0;
         ri[k] = i;
         rj[k] = j;
       }
       __syncthreads();
       auto upd_a = [&](int k, int l) {
         int ik = ri[k], jk = rj[k], il = ri[l], jl = rj[l];
-        if (ds[k] == 0.0 && ds[l] == 0.0) return;
+        if (act_k[k] == 0 && act_k[l] == 0) return;
         float2 ck = fc[k], sk = fs[k];
         float2 cl = fc[l], sl = fs[l];
         const float2 zero = make_float2(0.f, 0.f);
@@ -287,7 +287,7 @@ static __device__ int jacobi_df(int p, float2* A, float2* V, SdWs& w, double* re
       };
       auto upd_v = [&](int row, int l) {
         int il = ri[l], jl = rj[l];
-        if (jl < 0 || ds[l] == 0.0) return;
+        if (jl < 0 || act_k[l] == 0) return;
         float2 cl = fc[l], sl = fs[l];
         float2 vi = V[row * p + il], vj = V[row * p + jl];
         V[row * p + il] = df_add(df_mul(cl, vi), df_neg(df_mul(sl, vj)));
