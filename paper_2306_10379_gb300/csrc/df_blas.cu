@@ -246,6 +246,8 @@ __global__ void df_sum_parts_kernel(int nparts, const float2* parts, double* out
   if (threadIdx.x != 0) return;
   float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
   float m = 0.f;
+  // unrolled so that several partials are in flight at once (same order)
+#pragma unroll 8
   for (int b = 0; b < nparts; ++b) {
     t0 = df_add(t0, parts[2 * b]);
     t1 = df_add(t1, parts[2 * b + 1]);

@@ -1237,6 +1237,8 @@ __global__ void oz_gram_reduce_kernel(int p, int q, int nsplit, int nblk, int sy
     jj = t;
   }
   float2 s = make_float2(0.f, 0.f);
+  // unrolled so that several partials are in flight at once (same order)
+#pragma unroll 8
   for (int k = 0; k < nsplit; ++k) s = df_add(s, part[((size_t)k * nblk + b) * 4096 + ii * 64 + jj]);
   G[e] = df_to_double(s);
 }
@@ -1370,6 +1372,7 @@ __global__ void oz_gram_reduce_df_kernel(int p, int q, int nsplit, int nbj, cons
   int nblk = ((p + 63) / 64) * nbj;
   int ii = i - bi * 64, jj = j - bj * 64;
   float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
   for (int k = 0; k < nsplit; ++k) s = df_add(s, part[((size_t)k * nblk + b) * 4096 + ii * 64 + jj]);
   G[e] = s;
 }
