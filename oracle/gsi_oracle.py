@@ -18,7 +18,7 @@ this sign zeta_i = (V^T D^T A X V)_ii = (V^T D^T R V)_ii for tangent D (the
 paper's D_zeta of Eq. (CG_linesearch_D) after the sign flip), and
 zeta = beta for steepest descent (Eqs. (GTAY)-(GTG)).
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
   * stopping test ||R||_F / ||A||_2 <= tol, checked every iteration;
   * Brent-Dekker root finding on phi'(t) with tolerance 2 eps |t|, at most
     100 evaluations;
