@@ -10,7 +10,9 @@
 // two per row (gemm, left operand), per column (p x p right operand) or per
 // column and row chunk (gram: 64 rows in the mma.sync kernel, 256 or 128 in
 // the tcgen05 kernel):
-//   x = 2^(E-7) * sum_{i<7} d_i 2^(-7 i)   (truncation below 2^(E-49)).
+//   x = 2^(E-7) * sum_{i<7} d_i 2^(-7 i) + r,  |r| <= 2^(E-46) + 2^(E-50)
+// (the remainder below the last digit, and one rounding where the low word
+// of x joins the remainder after digit 2).
 // Digits are exact in bf16 and are stored with their weights, d_i 2^(-7 i);
 // products of two digits are exact in fp32, and the 28 digit pairs
 // (i + i' <= 6) are summed per "group" g = i + i' in fp32 accumulators whose

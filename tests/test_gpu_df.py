@@ -265,3 +265,56 @@ def test_oz_gram_tcgen05_and_mma_agree(G, n, p, q, sym):
     for o in outs:
         assert np.all(np.abs(o - ref) <= bound)
     assert np.all(np.abs(outs[0] - outs[1]) <= 2 * bound)
+
+
+def _place(torch, gsi, x, off):
+    """df64 copy of x on the device starting `off` float2 entries into a fresh
+    buffer (off = 1: 8 bytes past a 16-byte boundary)."""
+    d = gsi.to_df(x)
+    buf = torch.zeros(d.size + 2 * off, dtype=torch.float32, device="cuda")
+    view = buf[2 * off:].view(d.shape)
+    view.copy_(torch.from_numpy(d))
+    assert (view.data_ptr() % 16 == 0) == (off == 0)
+    return view
+
+
+@pytest.mark.parametrize("sym", [True, False])
+def test_oz_gram_unaligned_blocks(G, sym):
+    """Blocks that start 8 bytes past a 16-byte boundary take the tcgen05
+    Gram's 8-byte copy path: the same Gram as from aligned blocks, bit for
+    bit."""
+    torch, gsi = G
+    n, p = 3001, 64
+    rng = np.random.default_rng(77 + sym)
+    U = _exact(gsi, rng.standard_normal((n, p)))
+    V = U if sym else _exact(gsi, rng.standard_normal((n, p)))
+    outs = []
+    for off in (0, 1):
+        Ud = _place(torch, gsi, U, off)
+        Vd = Ud if sym else _place(torch, gsi, V, off)
+        Gm = torch.zeros((p, p), dtype=torch.float64, device="cuda")
+        gsi.oz_gram(Ud, Vd, Gm, sym=sym)
+        outs.append(Gm.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("fused,ne", [(True, 0), (False, 2)])
+def test_oz_gemm_unaligned_blocks(G, fused, ne):
+    """Operands and output 8 bytes past a 16-byte boundary: the tcgen05 block
+    product reads with 8-byte loads and finishes in its element-wise
+    epilogue, with the same result bit for bit."""
+    torch, gsi = G
+    n, p = 2001, 64
+    rng = np.random.default_rng(5 + ne)
+    U0 = _exact(gsi, rng.standard_normal((n, p)))
+    U1 = _exact(gsi, rng.standard_normal((n, p))) if fused else None
+    E = [_exact(gsi, rng.standard_normal((n, p))) for _ in range(ne)]
+    M = torch.from_numpy(rng.standard_normal((p, p))).cuda()
+    outs = []
+    for off in (0, 1):
+        out = _place(torch, gsi, np.zeros((n, p)), off)
+        gsi.oz_gemm(_place(torch, gsi, U0, off), M, out, s0=0.9,
+                    U1=_place(torch, gsi, U1, off) if fused else None, M1=M if fused else None,
+                    s1=0.2 if fused else 0.0, E=[_place(torch, gsi, e, off) for e in E], c=[0.5, -1.5][:ne])
+        outs.append(out.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
