@@ -49,9 +49,11 @@ gsi_status small_step(int mode, int p, const double* C, const double* B, const d
                       double* out, double* scratch, cudaStream_t st);
 // the same step with a float32 Jacobi eigensolver refined in df64 (small_df.cu)
 size_t small_df_scratch_bytes(int p);
+// modes 3 and 4 split mode 0 in two launches (eigenbasis of B; the rest),
+// passing (p + 1) p df64 values through eig_ws
 gsi_status small_step_df(int mode, int p, const double* C, const double* B, const double* Gam,
                          const double* Z, const double* XX, const double* XD, double* M,
-                         double* out, void* scratch, cudaStream_t st);
+                         double* out, void* scratch, cudaStream_t st, void* eig_ws = nullptr);
 // theta (descending) and U with C = U diag(theta) U^T, C symmetrised first.
 gsi_status small_eig(int p, const double* C, double* theta, double* U, double* scratch,
                      cudaStream_t st);

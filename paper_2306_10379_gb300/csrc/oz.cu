@@ -1380,13 +1380,14 @@ __global__ void oz_gram_reduce_df_kernel(int p, int q, int nsplit, int nbj, cons
 }
 
 gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bool sym, double* G,
-                   float2* scratch, cudaStream_t st, int nd, float2* Gdf) {
+                   float2* scratch, cudaStream_t st, int nd, float2* Gdf, int reserve_sms) {
   if (p < 1 || q < 1 || q > 128 || (sym && (p != q || Gdf)) || (nd != 3 && nd != ND) ||
       (!G && !Gdf) || (p > 128 && !Gdf))
     return GSI_ERR_ARG;
   const int nbj = (q + 63) / 64;
   const int nblk = oz_gram_blocks(p, q, sym);
-  const int ns = oz_gram_splits(n, p, q, sym);
+  int ns = oz_gram_splits(n, p, q, sym);
+  if (reserve_sms > 0) ns = std::max(1, std::min(ns, (sm_count() - reserve_sms) / nblk));
   const int tp = tensor_path();
   if (nd == ND && p <= 64 && q <= 64 && tp != 1) {
     // one 64 x 64 output block; every partial entry is written. 16-byte

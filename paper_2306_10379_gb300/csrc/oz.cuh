@@ -49,8 +49,10 @@ size_t oz_gram_scratch_bytes(int64_t n, int p, int q, bool sym);
 // fp32 sums, used by the mixed-precision mode). With Gdf non-null the result
 // is written as df64 to Gdf (p x q, any p; q <= 128): for symmetric A this is
 // the dense apply A X = A^T X.
+// reserve_sms: SMs left free for work running alongside on another stream.
 gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bool sym, double* G,
-                   float2* scratch, cudaStream_t st, int nd = 7, float2* Gdf = nullptr);
+                   float2* scratch, cudaStream_t st, int nd = 7, float2* Gdf = nullptr,
+                   int reserve_sms = 0);
 
 // df64 block helpers (df_blas.cu)
 gsi_status df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);

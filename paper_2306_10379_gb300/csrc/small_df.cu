@@ -22,7 +22,7 @@ constexpr int SD_THREADS = 1024;
 __global__ void __launch_bounds__(SD_THREADS)
 small_df_kernel(int mode, int p, const double* C, const double* B, const double* Gam,
                 const double* Z, const double* XX, const double* XD, double* M, double* out,
-                unsigned char* gws, int use_smem) {
+                unsigned char* gws, int use_smem, float2* eig) {
   extern __shared__ __align__(16) unsigned char sm_dyn[];
   __shared__ double red[SD_THREADS / 32];
   __shared__ int flag;
@@ -30,15 +30,15 @@ small_df_kernel(int mode, int p, const double* C, const double* B, const double*
   // use_smem: 1 = everything in shared memory, 2 = float32 part only
   SdWs w = use_smem == 1 ? sd_carve(sm_dyn, p) : use_smem == 2 ? sd_carve(gws, p, sm_dyn)
                                                                   : sd_carve(gws, p);
-  small_df_body(mode, p, C, B, Gam, Z, XX, XD, M, out, w, red, &flag, &sh_t);
+  small_df_body(mode, p, C, B, Gam, Z, XX, XD, M, out, w, red, &flag, &sh_t, eig);
 }
 
 size_t small_df_scratch_bytes(int p) { return sd_bytes(p); }
 
 gsi_status small_step_df(int mode, int p, const double* C, const double* B, const double* Gam,
                          const double* Z, const double* XX, const double* XD, double* M,
-                         double* out, void* scratch, cudaStream_t st) {
-  if (p < 1 || p > 128) return GSI_ERR_ARG;
+                         double* out, void* scratch, cudaStream_t st, void* eig_ws) {
+  if (p < 1 || p > 128 || ((mode == 3 || mode == 4) && !eig_ws)) return GSI_ERR_ARG;
   size_t bytes = sd_bytes(p);
   const size_t dfpart = 4 * (((size_t)p * p * sizeof(float2) + 15) & ~(size_t)15);
   int use_smem = bytes <= 200 * 1024 ? 1 : (bytes - dfpart <= 200 * 1024 ? 2 : 0);
@@ -47,7 +47,7 @@ gsi_status small_step_df(int mode, int p, const double* C, const double* B, cons
     GSI_CUDA_TRY(cudaFuncSetAttribute(small_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sm));
   small_df_kernel<<<1, SD_THREADS, sm, st>>>(mode, p, C, B, Gam, Z, XX, XD, M, out,
-                                             (unsigned char*)scratch, use_smem);
+                                             (unsigned char*)scratch, use_smem, (float2*)eig_ws);
   GSI_LAUNCH_CHECK();
   return GSI_OK;
 }

@@ -492,17 +492,32 @@ static __device__ int inv_sqrt_in_basis(int p, SdWs& w, double* M, int* flag) {
 // One p x p step for one problem, run by the whole calling block. mode 0:
 // eigenbasis of B, line-search coefficients, the step t of Alg. 3 and
 // M = S^{-1/2}; mode 1: M = B^{-1/2}; mode 2: eigenvectors of B (passed as
-// B) into M, eigenvalues into XD[0..p), unsorted. out: t, phi(t), Brent
-// evaluations, status (0 or 5), beta_max, cycle counts (5..12).
+// B) into M, eigenvalues into XD[0..p), unsorted. Mode 0 in two launches:
+// mode 3 only finds the eigenbasis of B and leaves V (p x p df64) and the
+// diagonal of V^T B V (p df64) in eig; mode 4 takes them from there and
+// does the rest. out: t, phi(t), Brent evaluations, status (0 or 5),
+// beta_max, cycle counts (5..12).
 static __device__ void small_df_body(int mode, int p, const double* C, const double* B,
                                      const double* Gam, const double* Z, const double* XX,
                                      const double* XD, double* M, double* out, SdWs& w, double* red,
-                                     int* flagp, double* sh_tp) {
+                                     int* flagp, double* sh_tp, float2* eig = nullptr) {
   double& sh_t = *sh_tp;
   const int q = p * p;
   long long t0 = clock64();
-  eig_refined(p, B, w, red, out + 8);
+  if (mode == 4) {
+    for (int e = threadIdx.x; e < q; e += blockDim.x) w.Vd[e] = eig[e];
+    for (int i = threadIdx.x; i < p; i += blockDim.x) w.Bd[i * p + i] = eig[q + i];
+    __syncthreads();
+  } else {
+    eig_refined(p, B, w, red, out + 8);
+  }
   long long t1 = clock64();
+  if (mode == 3) {
+    for (int e = threadIdx.x; e < q; e += blockDim.x) eig[e] = w.Vd[e];
+    for (int i = threadIdx.x; i < p; i += blockDim.x) eig[q + i] = w.Bd[i * p + i];
+    if (threadIdx.x == 0) out[5] = (double)(t1 - t0);
+    return;
+  }
   if (mode == 2) {
     // Rayleigh-Ritz: eigenvectors of C (here passed as B) into M (float64),
     // eigenvalues into XD[0..p) (unsorted; column i of M belongs to XD[i])
@@ -559,8 +574,9 @@ static __device__ void small_df_body(int mode, int p, const double* C, const dou
   int st = inv_sqrt_in_basis(p, w, M, flagp);
   if (threadIdx.x == 0) {
     out[3] = (double)st;
-    // cycles spent: eigenbasis, coefficients, line search, polar normaliser
-    out[5] = (double)(t1 - t0);
+    // cycles spent: eigenbasis (mode 3 wrote it), coefficients, line
+    // search, polar normaliser
+    if (mode != 4) out[5] = (double)(t1 - t0);
     out[6] = (double)(t3 - t1);
     out[7] = (double)(clock64() - t3);
   }

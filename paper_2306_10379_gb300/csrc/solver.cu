@@ -129,6 +129,13 @@ struct gsi_ctx {
   bool rinf_fused = false;   // the last block product also left max_r sum_j |R[r,j]| in dout[2]
   double* dots_ws = nullptr;
   double* small_ws = nullptr;
+  // the eigenbasis of D^T D runs on a second stream while the other
+  // line-search Grams run on st (one SM left to it); V and the diagonal pass
+  // through eig_ws
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_b = nullptr, ev_e = nullptr;
+  void* eig_ws = nullptr;
+  int gram_reserve = 0;  // SMs the next Grams leave free
   double* host = nullptr;  // pinned readback buffer
   std::vector<void*> allocs;
   // iteration state
@@ -247,7 +254,7 @@ gsi_status op_gram(gsi_ctx* c, const void* U, const void* V, bool sym, double* G
   gsi_status s;
   if (c->emu) {
     s = oz_gram(c->n, c->p, c->p, (const float2*)U, (const float2*)V, sym && U == V, G,
-                c->oz_gram_ws, c->st);
+                c->oz_gram_ws, c->st, 7, nullptr, c->gram_reserve);
     if (s == GSI_OK && sym && U != V) {
       symmetrize_kernel<<<ceil_div(c->p * c->p, 256), 256, 0, c->st>>>(c->p, G);
       note_launch();
@@ -328,7 +335,7 @@ gsi_status op_rowinf(gsi_ctx* c, const void* Rb) {
 gsi_status op_small(gsi_ctx* c, int mode, const double* B, const double* Zp) {
   prof_begin(c);
   gsi_status s = c->emu ? small_step_df(mode, c->p, c->Cm, B, c->Gm, Zp, c->XXm, c->XDm, c->Mm,
-                                        c->out, c->small_ws, c->st)
+                                        c->out, c->small_ws, c->st, c->eig_ws)
                         : small_step(mode, c->p, c->Cm, B, c->Gm, Zp, c->XXm, c->XDm, c->Mm, c->out,
                                      c->small_ws, c->st);
   prof_end(c, GSI_K_SMALL, 0.0, 0.0);
@@ -421,20 +428,33 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
   }
   GSI_TRY(op_matvec(c, Dp, c->W, false));
   GSI_TRY(op_gram(c, Dp, Dp, true, c->Bm));
-  GSI_TRY(op_gram(c, Dp, c->W, true, c->Gm));
+  // the eigenbasis of B = D^T D on the second stream, alongside the Grams below
+  const bool split = c->st2 != nullptr;
+  if (split) {
+    GSI_CUDA_TRY(cudaEventRecord(c->ev_b, c->st));
+    GSI_CUDA_TRY(cudaStreamWaitEvent(c->st2, c->ev_b, 0));
+    GSI_TRY(small_step_df(3, c->p, nullptr, c->Bm, nullptr, nullptr, nullptr, nullptr, nullptr, c->out,
+                          c->small_ws, c->st2, c->eig_ws));
+    GSI_CUDA_TRY(cudaEventRecord(c->ev_e, c->st2));
+    c->gram_reserve = 1;
+  }
+  gsi_status gs = op_gram(c, Dp, c->W, true, c->Gm);
   const double* Zp = c->Bm;
-  if (cg) {
-    GSI_TRY(op_gram(c, Dp, c->R, false, c->Zm));
+  if (gs == GSI_OK && cg) {
+    gs = op_gram(c, Dp, c->R, false, c->Zm);
     Zp = c->Zm;
   }
-  GSI_TRY(op_gram(c, c->X, c->X, true, c->XXm));
+  if (gs == GSI_OK) gs = op_gram(c, c->X, c->X, true, c->XXm);
+  c->gram_reserve = 0;
+  if (split) GSI_CUDA_TRY(cudaStreamWaitEvent(c->st, c->ev_e, 0));
+  GSI_TRY(gs);
   // X^T D in closed form from the measured X^T X: X^T R = (I - X^T X) C and
   // X^T P = K give X^T D = (I - X^T X)(C + b K) (b = 0 for SD and restarts)
   prof_begin(c);
   GSI_TRY(pp_axpby(c->p, 1.0, c->Cm, beta_used, beta_used != 0.0 ? c->Km : nullptr, c->Gm2, c->st));
   GSI_TRY(pp_gemm(c->p, -1.0, c->XXm, c->Gm2, 1.0, c->Gm2, c->XDm, c->st));
   prof_end(c, GSI_K_SMALL, 0.0, 0.0);
-  GSI_TRY(op_small(c, 0, c->Bm, Zp));
+  GSI_TRY(op_small(c, split ? 4 : 0, c->Bm, Zp));
   GSI_TRY(readback(c, c->out, 5));
   const double t = c->host[0];
   c->last_t = t;
@@ -659,6 +679,12 @@ const char* gsi_last_error(void) { return g_last_error; }
 gsi_status gsi_destroy(gsi_ctx* c) {
   if (!c) return GSI_ERR_ARG;
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->st2) {
+    cudaStreamSynchronize(c->st2);
+    cudaStreamDestroy(c->st2);
+  }
+  if (c->ev_b) cudaEventDestroy(c->ev_b);
+  if (c->ev_e) cudaEventDestroy(c->ev_e);
   prof_harvest(c);
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
@@ -804,6 +830,12 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
     }
     CK(dev_alloc(c, (void**)&c->small_ws, std::max(small_scratch_doubles(p) * sizeof(double),
                                                    small_df_scratch_bytes(p))));
+    if (c->emu) {
+      CK(dev_alloc(c, &c->eig_ws, (size_t)(q + p) * sizeof(float2)));
+      CK(cuda_status_ok(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking)));
+      CK(cuda_status_ok(cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming)));
+      CK(cuda_status_ok(cudaEventCreateWithFlags(&c->ev_e, cudaEventDisableTiming)));
+    }
     CK(cuda_status_ok(cudaMallocHost((void**)&c->host, std::max<size_t>(q, 64) * sizeof(double))));
     if (opts.anorm > 0) {
       c->anorm = opts.anorm;
