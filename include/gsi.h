@@ -321,6 +321,14 @@ gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, 
 gsi_status gsi_set_tensor_path(int32_t path);
 int32_t gsi_tensor_path(void);
 
+/* Measured multiply-add throughput of this GPU (no counterpart in the paper;
+ * the denominators behind the choice of df64 and tensor-core digits):
+ * out[0] = float64 FMA TFLOP/s, out[1] = float32 FMA TFLOP/s, each the best
+ * of three ~50 ms launches of 8 independent FMA chains per thread over
+ * 8 blocks per SM (2 flops per FMA). out: 2 host doubles. Allocates and
+ * frees a small device buffer on `stream`; synchronises it. */
+gsi_status gsi_measure_fma_peaks(double* out, void* stream);
+
 /* ---- batched solver -------------------------------------------------------
  * Many independent problems, each the dominant p_i-dimensional invariant
  * subspace of a symmetric A_i (the problem of Sec. 2.1), iterated together

@@ -29,7 +29,7 @@ EXPORTED = [
     "gsi_csr_to_sell", "gsi_spmm_sell", "gsi_gram", "gsi_residual", "gsi_linesearch",
     "gsi_retract", "gsi_df_spmm_csr", "gsi_oz_gemm", "gsi_oz_gram", "gsi_reset",
     "gsi_profile_enable", "gsi_profile_read", "gsi_launch_count", "gsi_oz_dense_apply",
-    "gsi_oz_gram_noalloc",
+    "gsi_oz_gram_noalloc", "gsi_measure_fma_peaks",
 ]
 
 
@@ -147,6 +147,8 @@ def _lib():
         L.gsi_set_tensor_path.restype = ctypes.c_int
         L.gsi_tensor_path.argtypes = []
         L.gsi_tensor_path.restype = ctypes.c_int32
+        L.gsi_measure_fma_peaks.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.gsi_measure_fma_peaks.restype = ctypes.c_int
         L.gsi_mlp_num_params.argtypes = [i32, i32, i32]
         L.gsi_mlp_num_params.restype = ctypes.c_int64
         _LIB = L
@@ -267,12 +269,20 @@ def retract(t, M, X, D, Y, W, stream=None):
 
 
 def set_tensor_path(path):
-    """0: tcgen05 kernels where faster (default); 1: mma.sync only; 2: tcgen05 wherever they apply."""
+    """0 (default) and 2: tcgen05 kernels wherever they apply (p, q <= 64); 1: mma.sync only."""
     _check(lib().gsi_set_tensor_path(int(path)), "gsi_set_tensor_path")
 
 
 def tensor_path():
     return int(lib().gsi_tensor_path())
+
+
+def measure_fma_peaks(stream=None):
+    """Measured float64 and float32 multiply-add throughput of the current GPU (TFLOP/s)."""
+    out = np.zeros(2, np.float64)
+    _check(lib().gsi_measure_fma_peaks(ctypes.c_void_p(out.ctypes.data), _stream(stream)),
+           "gsi_measure_fma_peaks")
+    return {"fp64_fma_tflops": float(out[0]), "fp32_fma_tflops": float(out[1])}
 
 
 def launch_count():

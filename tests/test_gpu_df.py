@@ -318,3 +318,13 @@ def test_oz_gemm_unaligned_blocks(G, fused, ne):
                     s1=0.2 if fused else 0.0, E=[_place(torch, gsi, e, off) for e in E], c=[0.5, -1.5][:ne])
         outs.append(out.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_fma_peaks_are_measured(G):
+    """The float64 / float32 FMA throughput probe returns finite rates, the
+    float32 pipe well ahead of the float64 one (the premise of the df64
+    design)."""
+    torch, gsi = G
+    pk = gsi.measure_fma_peaks()
+    assert np.isfinite(pk["fp64_fma_tflops"]) and pk["fp64_fma_tflops"] > 0
+    assert pk["fp32_fma_tflops"] > 4 * pk["fp64_fma_tflops"]
