@@ -314,7 +314,7 @@ gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, 
  * 1 the mma.sync kernels everywhere. Block products are identical on both
  * (same digits, exact integer digit-pair sums, same combination order).
  * Grams agree to float64-class accuracy but not bit for bit: the tcgen05
- * Gram takes its column exponents over 256-row (U == V) or 128-row chunks,
+ * Gram takes its column exponents over 256-row (U == V) or 160-row chunks,
  * the mma.sync Gram over 64-row chunks. The switch exists to compare them.
  * Process-wide; the environment variable GSI_TENSOR_PATH=mma or =tcgen05
  * selects 1 or 2 before the first product. */

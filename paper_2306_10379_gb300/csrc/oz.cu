@@ -8,7 +8,7 @@
 // Block data is df64 (float2 = hi, lo). Every operand is cut into ND = 7
 // signed "digits" d_i in [-128, 128] on a fixed-point grid set by a power of
 // two per row (gemm, left operand), per column (p x p right operand) or per
-// column and row chunk (gram: 64 rows in the mma.sync kernel, 256 or 128 in
+// column and row chunk (gram: 64 rows in the mma.sync kernel, 256 or 160 in
 // the tcgen05 kernel):
 //   x = 2^(E-7) * sum_{i<7} d_i 2^(-7 i) + r,  |r| <= 2^(E-46) + 2^(E-50)
 // (the remainder below the last digit, and one rounding where the low word
@@ -935,7 +935,7 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
 
 // ---------------------------------------------------------------------------
 // oz_gram on the 5th-generation tensor cores, for p, q <= 64 and the 7-digit
-// split. Rows go in exponent chunks of EC rows (256 for U == V, 128
+// split. Rows go in exponent chunks of EC rows (256 for U == V, 160
 // otherwise), staged raw in shared memory by cp.async; the column exponents
 // are taken over the whole chunk, and the chunk's digit-pair products are
 // summed in tensor memory over its sub-chunks of SK rows (32, resp. 16) before
@@ -962,13 +962,28 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
 constexpr int TG_WORKERS = 512;
 constexpr int TG_THREADS = TG_WORKERS + 32;
 constexpr int TG_RS = 66;              // raw row stride in float2 (528 B: rows on 16 B)
-constexpr int TG_RAW_ROWS = 256;       // U == V: 256 rows of U; else 128 of U, then 128 of V
-constexpr uint32_t TG_DBUF = 32768;    // one digit buffer (A planes, B planes or pad)
+// Chunk geometry: U == V: 256-row exponent chunks in 32-row sub-chunks, raw
+// stage 256 rows, digit buffers of 7 planes + a pad plane (32 KB); U != V:
+// 160-row chunks in 16-row sub-chunks, raw stage 160 rows of U then 160 of
+// V, digit buffers of 7 + 7 planes (28 KB). Per row a stacked accumulator
+// gains at most 4 * 128 * 72 < 28800 < 2^24 / 256, so both stay exact.
+template <bool SYM>
+struct TgGeom {
+  static constexpr int EC = SYM ? 256 : 160;
+  static constexpr int SK = SYM ? 32 : 16;
+  static constexpr int RAWR = SYM ? EC : 2 * EC;    // raw stage rows
+  static constexpr int NG = RAWR / 32;              // 32-row groups of the maxima pass
+  static constexpr uint32_t DBUF = SYM ? 32768u : 28672u;
+  static constexpr size_t smem() {
+    return (size_t)RAWR * TG_RS * sizeof(float2) + 2 * DBUF + NG * 64 * sizeof(float) + 128 * sizeof(int) +
+           64;
+  }
+};
+static_assert(TgGeom<true>::smem() <= 227 * 1024 && TgGeom<false>::smem() <= 227 * 1024, "shared memory");
+static_assert(TgGeom<false>::EC % (2 * TgGeom<false>::SK) == 0 && TgGeom<true>::EC % (2 * TgGeom<true>::SK) == 0,
+              "an even number of sub-chunks per chunk");
 
-size_t oz_gram_tc_smem() {
-  return (size_t)TG_RAW_ROWS * TG_RS * sizeof(float2) + 2 * TG_DBUF + 8 * 64 * sizeof(float) +
-         128 * sizeof(int) + 64;
-}
+size_t oz_gram_tc_smem(bool sym) { return sym ? TgGeom<true>::smem() : TgGeom<false>::smem(); }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -980,12 +995,14 @@ template <bool SYM>
 __global__ void __launch_bounds__(TG_THREADS, 1)
 oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
                   int vec16, float2* part) {
-  constexpr int EC = SYM ? 256 : 128, SK = SYM ? 32 : 16, NSUB = EC / SK;
+  using Geo = TgGeom<SYM>;
+  constexpr int EC = Geo::EC, SK = Geo::SK, NSUB = EC / SK, RAWR = Geo::RAWR, NG = Geo::NG;
+  constexpr uint32_t TG_DBUF = Geo::DBUF;
   constexpr uint32_t plane = 64u * SK * 2;  // one digit plane: 64 columns x SK rows, bf16
   extern __shared__ __align__(16) unsigned char tg_smem[];
   float2* raw = reinterpret_cast<float2*>(tg_smem);
-  unsigned char* dig = tg_smem + (size_t)TG_RAW_ROWS * TG_RS * sizeof(float2);
-  float* cmx = reinterpret_cast<float*>(dig + 2 * TG_DBUF);  // [8][64] partial column maxima
+  unsigned char* dig = tg_smem + (size_t)RAWR * TG_RS * sizeof(float2);
+  float* cmx = reinterpret_cast<float*>(dig + 2 * TG_DBUF);  // [NG][64] partial column maxima
   int* Eu = reinterpret_cast<int*>(cmx + 8 * 64);
   int* Ev = Eu + 64;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Ev + 64);     // one per digit buffer
@@ -1030,25 +1047,25 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   bool failed = false;
   const int64_t nchunks = (n + EC - 1) / EC;
 
-  // raw rows of chunk ch (workers): U rows (256, or 128 then V's 128),
+  // raw rows of chunk ch (workers): U rows (256, or 160 then V's 160),
   // zero-filled outside the matrix
   auto stage = [&](int64_t ch) {
     const int64_t r0 = ch * EC;
     if (vec16) {
-      for (int e = tid; e < TG_RAW_ROWS * 32; e += TG_WORKERS) {
+      for (int e = tid; e < RAWR * 32; e += TG_WORKERS) {
         const int row = e >> 5, c = 2 * (e & 31);
-        const bool isv = !SYM && row >= 128;
-        const int64_t R = r0 + (isv ? row - 128 : row);
+        const bool isv = !SYM && row >= EC;
+        const int64_t R = r0 + (isv ? row - EC : row);
         const int ld = isv ? q : p;
         const float2* src = isv ? V : U;
         const bool ok = R < n && c < ld;
         cp_async16(raw + row * TG_RS + c, src + (ok ? R * ld + c : 0), ok);
       }
     } else {
-      for (int e = tid; e < TG_RAW_ROWS * 64; e += TG_WORKERS) {
+      for (int e = tid; e < RAWR * 64; e += TG_WORKERS) {
         const int row = e >> 6, c = e & 63;
-        const bool isv = !SYM && row >= 128;
-        const int64_t R = r0 + (isv ? row - 128 : row);
+        const bool isv = !SYM && row >= EC;
+        const int64_t R = r0 + (isv ? row - EC : row);
         const int ld = isv ? q : p;
         const float2* src = isv ? V : U;
         const bool ok = R < n && c < ld;
@@ -1066,24 +1083,26 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   const int loc = SYM ? tid : (tid & 255);
   const int ic = 8 * ((loc >> 5) & 7) + (lane & 7);
   const int iq = 2 * (((lane >> 4) & 1) + 2 * (loc >> 8)) + ((lane >> 3) & 1);
-  const int irow = (isv ? 128 : 0) + 4 * iq;
+  const int irow = (isv ? EC : 0) + 4 * iq;
 
   if (!issuer && (int64_t)blockIdx.x < nchunks) stage(blockIdx.x);
   for (int64_t ch = blockIdx.x; ch < nchunks && !failed; ch += gridDim.x) {
     if (!issuer) cp_async_wait_all();
     __syncthreads();
     // (a) column maxima of |hi| over the chunk: thread -> column c, 32 rows
-    // of raw row group g (g < 4: U, else V when U != V)
+    // of raw row group g (g < NG / 2: U, else V when U != V)
     if (!issuer) {
-      const int c = tid & 63, g = tid >> 6;
-      float mx = 0.f;
+      const int c = tid & 63;
+      for (int g = tid >> 6; g < NG; g += TG_WORKERS / 64) {
+        float mx = 0.f;
 #pragma unroll 8
-      for (int k = 0; k < 32; ++k) mx = fmaxf(mx, fabsf(raw[(32 * g + k) * TG_RS + c].x));
-      cmx[g * 64 + c] = mx;
+        for (int k = 0; k < 32; ++k) mx = fmaxf(mx, fabsf(raw[(32 * g + k) * TG_RS + c].x));
+        cmx[g * 64 + c] = mx;
+      }
     }
     __syncthreads();
     if (tid < (SYM ? 64 : 128)) {
-      const int c = tid & 63, g0 = (tid < 64) ? 0 : 4, ng = SYM ? 8 : 4;
+      const int c = tid & 63, g0 = (tid < 64) ? 0 : NG / 2, ng = SYM ? NG : NG / 2;
       float m = 0.f;
       for (int g = g0; g < g0 + ng; ++g) m = fmaxf(m, cmx[g * 64 + c]);
       if (tid < 64) Eu[c] = exponent_above(m);
@@ -1393,7 +1412,7 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
     // one 64 x 64 output block; every partial entry is written. 16-byte
     // copies need even row lengths and 16-byte aligned bases.
     const bool vec16 = ((p | q) & 1) == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)V & 15) == 0;
-    const size_t tsm = oz_gram_tc_smem();
+    const size_t tsm = oz_gram_tc_smem(sym);
     auto kern = sym ? oz_gram_tc_kernel<true> : oz_gram_tc_kernel<false>;
     GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
     kern<<<ns, TG_THREADS, tsm, st>>>(n, p, q, U, V, vec16 ? 1 : 0, scratch);

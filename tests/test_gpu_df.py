@@ -105,7 +105,7 @@ def test_oz_gemm_in_place(G):
 def _gram_bound(U, V, rows=256):
     """Error bound of the digit-split Gram: per chunk of `rows` rows every
     product is cut at 2^-49 of the chunk's column maxima. Chunks of 256 rows
-    bound the 64-row chunks of the mma.sync kernel and the 256/128-row chunks
+    bound the 64-row chunks of the mma.sync kernel and the 256/160-row chunks
     of the tcgen05 kernel alike (a sub-chunk's maxima are at most its
     chunk's)."""
     n, p = U.shape
@@ -242,7 +242,7 @@ def test_oz_gemm_tcgen05_equals_mma(G, n, p, fused, ne):
 @pytest.mark.parametrize("n,p,q,sym", [(100003, 64, 64, True), (100003, 64, 64, False), (4097, 17, 40, False),
                                        (70, 8, 8, True), (200000, 48, 5, False)])
 def test_oz_gram_tcgen05_and_mma_agree(G, n, p, q, sym):
-    """The tcgen05 Gram (256/128-row exponent chunks, tensor-memory group
+    """The tcgen05 Gram (256/160-row exponent chunks, tensor-memory group
     sums) and the mma.sync one (64-row chunks) are different roundings of the
     same exact Gram: each within the digit-split bound of the oracle, and
     within the sum of the two bounds of each other, on rows whose magnitudes
