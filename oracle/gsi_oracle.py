@@ -32,7 +32,11 @@ Readings of points the paper leaves open:
   * zeta is taken from D^T R, and the polar factor from the measured Gram of
     X + tD (both equal the paper's expressions in exact arithmetic);
   * AX is recomputed explicitly when t*sqrt(beta_max) < 1e3*eps, every
-    `recompute_every` iterations, and before the final residual.
+    `recompute_every` iterations, and before the final residual;
+  * LOBCG (the comparator of Sec. 7): the basis of span(X_k, G_k, X_{k-1}) is
+    built block by block with rank truncation at 1e-10 of each block's norm
+    (the paper's footnote leaves the replacement of X_{k-1} open); the
+    Rayleigh-Ritz matrix Q^T A Q is formed explicitly (the paper's LOBCG(+)).
 """
 from __future__ import annotations
 
@@ -406,6 +410,64 @@ def solve(A, X0, opts: Options, record=False, callback=None):
         P, R_prev, rr_prev = D, R, rr
         k += 1
     return Result(X, Y, k, matvecs, converged, rel, restarts, history)
+
+
+# ---------------------------------------------------------------------------
+# LOBCG comparator (Sec. 7, "Comparison to LOBCG"; Knyazev 2001)
+# ---------------------------------------------------------------------------
+
+def block_basis(blocks, rank_tol=1e-10):
+    """Orthonormal basis of the column span of the blocks, built block by
+    block: each block is projected off the basis so far (twice), and its left
+    singular vectors with singular values above rank_tol times the block's
+    own norm are appended. Near convergence X_{k-1} lies almost in span(X_k),
+    the cancellation of the paper's footnote to Eq. (def_Vk_LOBPCG); the
+    truncation drops what is left of it at rounding level."""
+    Q = np.zeros((blocks[0].shape[0], 0))
+    for B in blocks:
+        bn = np.linalg.norm(B, 2)
+        if bn == 0.0:
+            continue
+        for _ in range(2):
+            B = B - Q @ (Q.T @ B)
+        U, s, _ = np.linalg.svd(B, full_matrices=False)
+        Q = np.hstack([Q, U[:, s > rank_tol * bn]])
+    return Q
+
+
+def lobcg_step(A, X, X_prev=None):
+    """One LOBCG step: the Rayleigh-Ritz procedure for A on
+    V_k = span(X_k, G_k, X_{k-1}) (Eq. (def_Vk_LOBPCG)), G_k = A X_k - X_k C_k
+    the gradient direction; the next iterate is the Ritz vectors of the p
+    largest Ritz values (the maximisation of the partial trace; the minimum
+    problem runs on -A as in Sec. 2.1)."""
+    Y = spmm(A, X)
+    C = gram(X, Y)
+    G = Y - X @ (0.5 * (C + C.T))
+    Q = block_basis([X, G] + ([X_prev] if X_prev is not None else []))
+    H = gram(Q, spmm(A, Q))
+    w, V = np.linalg.eigh(0.5 * (H + H.T))
+    return Q @ V[:, np.argsort(w)[::-1][:X.shape[1]]]
+
+
+def lobcg_solve(A, X0, tol=1e-8, anorm=0.0, max_iters=10000):
+    """LOBCG from the orthonormalised X0: X_{k+1} = lobcg_step(A, X_k, X_{k-1})
+    (no X_{-1} in the first step), with the stopping test of solve():
+    ||A X_k - X_k C_k||_F <= tol * anorm."""
+    anorm = anorm if anorm > 0 else anorm_inf(A)
+    X = orthonormalize(X0)
+    X_prev = None
+    k = 0
+    while True:
+        Y = spmm(A, X)
+        C = gram(X, Y)
+        R = residual(X, Y, 0.5 * (C + C.T))
+        rel = math.sqrt(float(np.sum(R * R))) / anorm
+        if rel <= tol or k >= max_iters:
+            break
+        X, X_prev = lobcg_step(A, X, X_prev), X
+        k += 1
+    return Result(X, Y, k, k + 1, rel <= tol, rel, 0)
 
 
 # ---------------------------------------------------------------------------
