@@ -45,6 +45,16 @@ NCU_TRAFFIC = {
 }
 
 
+FP64_FMA_TFLOPS = 1.25  # measured float64 FMA throughput of this GPU (profiles/fma_peaks_gb300.md)
+
+
+def _class_entry(v):
+    e = {"launches": v["launches"], "ms_total": v["ms"]}
+    if v.get("flops", 0.0) > 0.0 and v["ms"] > 0.0:
+        e["fp64_class_tflops"] = v["flops"] / (v["ms"] * 1e-3) / 1e12
+    return e
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,7 +532,11 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
                 else "fallback 6.8 TB/s",
                 "launch_ms": avg_ms, "alg_bytes_per_launch": bytes_per,
-                "classes": {k: {"launches": v["launches"], "ms_total": v["ms"]} for k, v in prof.items()}}
+                "classes": {k: _class_entry(v) for k, v in prof.items()},
+                # the digit-product classes run float64-class products; their rate in
+                # float64 flops (2 n p^2 per Gram, 2 n p^2 nk per block product) next to
+                # the measured float64 FMA peak (profiles/fma_peaks_gb300.md)
+                "fp64_fma_peak_tflops": FP64_FMA_TFLOPS}
 
     # the block matvec (SpMM) against the HBM roofline
     sp = prof.get("spmm", {"launches": 0})
