@@ -155,6 +155,24 @@ gsi_status gsi_reset(gsi_ctx* ctx, const double* X0, int32_t X0_on_device);
  * until the next call on ctx. For tests and benchmarks. */
 gsi_status gsi_state_ptrs(gsi_ctx* ctx, void** X, void** Y);
 
+/* Bounded device waits (no counterpart in the paper). The tensor-core
+ * kernels wait on their own products with an iteration limit instead of
+ * spinning without end; a wait that runs out drains the tensor core (every
+ * product already issued completes before the kernel releases its tensor
+ * memory and returns), leaves non-finite outputs and adds one to a
+ * process-wide count. gsi_solve, gsi_step, gsi_reset and gsi_create then
+ * return GSI_ERR_TIMEOUT instead of the status the non-finite values would
+ * cause.
+ * gsi_set_wait_limit: polls allowed to each wait on a batch of products,
+ *   0 .. 2^24, on the current device; a negative value restores the default
+ *   2^24. The drain itself always allows 2^24 polls. A small limit forces
+ *   the timeout path (tests); the default is far above any product's
+ *   latency.
+ * gsi_device_timeouts: the current device's count of waits that ran out
+ *   since the library was loaded (synchronises the legacy default stream). */
+gsi_status gsi_set_wait_limit(int32_t polls);
+gsi_status gsi_device_timeouts(int64_t* count);
+
 /* Kernel classes for gsi_profile_read. */
 typedef enum {
   GSI_K_SPMM = 0,      /* block matvec A*Z */
@@ -301,7 +319,9 @@ gsi_status gsi_oz_dense_apply(int64_t n, int32_t p, const float* A, const float*
  * process exits; calls whose partials would exceed it (more than 256 SMs)
  * return GSI_ERR_ARG with a message in gsi_last_error(). The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. Every
+ * that device current; make that first call before any stream capture. The
+ * looked-up address is kept for the life of the process, so the device's
+ * primary context must not be reset (cudaDeviceReset) between calls. Every
  * call shares the array and overwrites it (it is cleared on each call), so
  * calls whose work overlaps on the GPU -- on different streams, or from
  * different threads -- race; serialise them. No cudaMalloc, cudaFree or

@@ -33,7 +33,7 @@ Readings of points the paper leaves open:
     X + tD (both equal the paper's expressions in exact arithmetic);
   * AX is recomputed explicitly when t*sqrt(beta_max) < 1e3*eps, every
     `recompute_every` iterations, and before the final residual;
-  * LOBCG (the comparator of Sec. 7): the basis of span(X_k, G_k, X_{k-1}) is
+  * LOBCG (the comparator of Sec. 6.4): the basis of span(X_k, G_k, X_{k-1}) is
     built block by block with rank truncation at 1e-10 of each block's norm
     (the paper's footnote leaves the replacement of X_{k-1} open); the
     Rayleigh-Ritz matrix Q^T A Q is formed explicitly (the paper's LOBCG(+)).
@@ -413,7 +413,7 @@ def solve(A, X0, opts: Options, record=False, callback=None):
 
 
 # ---------------------------------------------------------------------------
-# LOBCG comparator (Sec. 7, "Comparison to LOBCG"; Knyazev 2001)
+# LOBCG comparator (Sec. 6.4, "Comparison to LOBCG"; Knyazev 2001)
 # ---------------------------------------------------------------------------
 
 def block_basis(blocks, rank_tol=1e-10):

@@ -4,6 +4,8 @@
 // that forbid allocation after start-up, or hosts whose allocator is not
 // reachable from the calling thread. The per-block partial sums live in one
 // file-scope __device__ array instead of a cudaMalloc'd buffer.
+#include <atomic>
+
 #include "oz.cuh"
 
 namespace gsi {
@@ -17,7 +19,12 @@ static __device__ __align__(256) float2 g_gram_scratch[NOALLOC_SCRATCH_BYTES / s
 
 namespace {
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
+// Device address of g_gram_scratch per device. Threads making their first
+// call on a device at the same time all store the same value, so relaxed
+// atomics suffice. The cache assumes the device's primary context lives until
+// the process exits: after a cudaDeviceReset the next context places the
+// array anew, and the cached address would be stale.
+std::atomic<void*> g_scratch_addr[kMaxDevices] = {};
 }  // namespace
 
 }  // namespace gsi
@@ -38,12 +45,11 @@ extern "C" gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const
   if (dev < 0 || dev >= kMaxDevices) return GSI_ERR_ARG;
   // The array's name is a host-side stand-in in host code; the device address
   // is looked up once per device, with that device current.
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
+  void* ptr = g_scratch_addr[dev].load(std::memory_order_relaxed);
+  if (!ptr) {
     GSI_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_gram_scratch));
-    g_scratch_addr[dev] = ptr;
+    g_scratch_addr[dev].store(ptr, std::memory_order_relaxed);
   }
   return oz_gram(n, p, q, reinterpret_cast<const float2*>(U), reinterpret_cast<const float2*>(V),
-                 sym != 0, G, reinterpret_cast<float2*>(g_scratch_addr[dev]),
-                 (cudaStream_t)stream);
+                 sym != 0, G, reinterpret_cast<float2*>(ptr), (cudaStream_t)stream);
 }

@@ -400,6 +400,10 @@ constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr int TC_WAIT_LIMIT = 1 << 24;
 
 __device__ int g_oz_tc_timeouts;  // count of bounded waits that ran out
+// polls allowed to a wait on the products of a tile or sub-chunk (host-settable,
+// 0..TC_WAIT_LIMIT); the drain after a wait that ran out always polls up to
+// TC_WAIT_LIMIT times
+__device__ int g_oz_wait_limit = TC_WAIT_LIMIT;
 
 __host__ __device__ inline size_t tc_plane_bytes(int rows, int K16) { return (size_t)rows * K16 * 2; }
 
@@ -428,9 +432,9 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, int limit = TC_WAIT_LIMIT) {
   uint32_t done = 0;
-  for (int it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
+  for (int it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
         "selp.b32 %0, 1, 0, P1;\n}\n"
@@ -439,6 +443,18 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
         : "memory");
   }
   return done != 0;
+}
+
+// After a wait ran out: the issuing thread commits once more to the drain
+// barrier, which completes when every product it has issued so far has
+// completed (a commit tracks all earlier tcgen05 operations of its thread);
+// every thread then waits for that with the full bound, so no product is in
+// flight when the tensor memory is released.
+__device__ __forceinline__ void tc_drain(bool issuing_thread, uint32_t mbd) {
+  if (issuing_thread)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbd)
+                 : "memory");
+  tc_wait(mbd, 0u, TC_WAIT_LIMIT);
 }
 
 __device__ __forceinline__ void tc_ld4(uint32_t r[4], uint32_t taddr) {
@@ -458,8 +474,8 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   unsigned char* Bd = Ad + ND * aplane;
   int* Er = reinterpret_cast<int*>(Bd + ND * bplane);
   int* Fs = Er + TC_M;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Fs + 64);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Fs + 64);  // [0] products, [1] drain
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool two = a.fuse_u1 != 0;
 
@@ -477,8 +493,10 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + 1)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  const int wait_limit = g_oz_wait_limit;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -598,7 +616,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
       }
     };
     if (rowwise && !issuer) fetch_row(0);
-    const bool done = issuer || tc_wait(mb, phase);
+    const bool done = issuer || tc_wait(mb, phase, wait_limit);
     phase ^= 1u;
     if (__syncthreads_or(!done)) {
       failed = true;
@@ -706,11 +724,11 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     __syncthreads();
   }
   if (failed) {
-    // a product that did not complete: count it, wait once more for the
-    // tensor core (bounded), poison this block's rows so the caller sees
-    // non-finite values, and release the tensor memory
+    // a product that did not complete in time: count it, drain the tensor
+    // core (bounded), poison this block's rows so the caller sees non-finite
+    // values, and release the tensor memory
     if (tid == 0) atomicAdd(&g_oz_tc_timeouts, 1);
-    tc_wait(mb, phase ^ 1u);
+    tc_drain(issuer && lane == 0, smem_addr(mbar + 1));
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
       for (int e = tid; e < TC_M * NC; e += TC_THREADS) {
         const int64_t R = tile * TC_M + e / NC;
@@ -996,10 +1014,10 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   float2* raw = reinterpret_cast<float2*>(tg_smem);
   unsigned char* dig = tg_smem + (size_t)RAWR * TG_RS * sizeof(float2);
   float* cmx = reinterpret_cast<float*>(dig + 2 * TG_DBUF);  // [NG][64] partial column maxima
-  int* Eu = reinterpret_cast<int*>(cmx + 8 * 64);
+  int* Eu = reinterpret_cast<int*>(cmx + NG * 64);  // after all NG groups of maxima
   int* Ev = Eu + 64;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Ev + 64);     // one per digit buffer
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Ev + 64);     // one per digit buffer, then the drain
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool issuer = warp == TG_WORKERS / 32;
   // the pad plane after the 7 planes of U (U == V) is read by the bottom half
@@ -1017,12 +1035,14 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + 1)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + 2)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
+  const int wait_limit = g_oz_wait_limit;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
                          ((uint32_t)(128 >> 4) << 24);
   const uint32_t dbase = smem_addr(dig);
@@ -1107,7 +1127,7 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
       const int buf = s & 1;
       bool ok = true;
       if (s >= 2) {  // the products of sub-chunk s - 2 read this buffer
-        if (!issuer) ok = tc_wait(buf ? mb1 : mb0, buf ? ph1 : ph0);
+        if (!issuer) ok = tc_wait(buf ? mb1 : mb0, buf ? ph1 : ph0, wait_limit);
         if (buf) ph1 ^= 1u;
         else ph0 ^= 1u;
       }
@@ -1159,8 +1179,8 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
     // (c) the last two sub-chunks' products, then the combination
     bool ok = true;
     if (!issuer) {
-      ok = tc_wait(mb0, ph0);
-      ok = tc_wait(mb1, ph1) && ok;
+      ok = tc_wait(mb0, ph0, wait_limit);
+      ok = tc_wait(mb1, ph1, wait_limit) && ok;
     }
     ph0 ^= 1u;
     ph1 ^= 1u;
@@ -1197,13 +1217,10 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   }
   if (!issuer) cp_async_wait_all();
   if (failed) {
-    // a product that did not complete: count it, wait once more (bounded)
-    // for the tensor core, and report non-finite partial sums
+    // a product that did not complete in time: count it, drain the tensor
+    // core (bounded), and report non-finite partial sums
     if (tid == 0) atomicAdd(&g_oz_tc_timeouts, 1);
-    if (!issuer) {
-      tc_wait(mb0, ph0);
-      tc_wait(mb1, ph1);
-    }
+    tc_drain(issuer && lane == 0, smem_addr(mbar + 2));
 #pragma unroll
     for (int e = 0; e < 16; ++e) res[e] = make_float2(NAN, NAN);
   }
@@ -1352,6 +1369,17 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   if (nparts) *nparts = gx * ncs;
   kern<<<dim3(gx, ncs), GM_THREADS, smem, st>>>(n, p, p16, K16, a);
   GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
+gsi_status oz_set_wait_limit(int limit) {
+  const int v = (limit < 0 || limit > TC_WAIT_LIMIT) ? TC_WAIT_LIMIT : limit;
+  GSI_CUDA_TRY(cudaMemcpyToSymbol(g_oz_wait_limit, &v, sizeof(int)));
+  return GSI_OK;
+}
+
+gsi_status oz_timeouts_async(int* host_dst, cudaStream_t st) {
+  GSI_CUDA_TRY(cudaMemcpyFromSymbolAsync(host_dst, g_oz_tc_timeouts, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
   return GSI_OK;
 }
 

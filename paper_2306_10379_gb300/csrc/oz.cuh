@@ -54,6 +54,13 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
                    float2* scratch, cudaStream_t st, int nd = 7, float2* Gdf = nullptr,
                    int reserve_sms = 0);
 
+// Bounded waits of the tcgen05 kernels: polls allowed to a wait on a batch of
+// products (limit < 0: the default, 2^24); a wait that runs out drains the
+// tensor core, counts one timeout and leaves non-finite outputs.
+gsi_status oz_set_wait_limit(int limit);
+// enqueue a copy of the process-wide timeout count into host_dst (pinned)
+gsi_status oz_timeouts_async(int* host_dst, cudaStream_t st);
+
 // df64 block helpers (df_blas.cu)
 gsi_status df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);
 gsi_status df_to_f64(int64_t count, const float2* x, double* y, cudaStream_t st);

@@ -137,6 +137,8 @@ struct gsi_ctx {
   void* eig_ws = nullptr;
   int gram_reserve = 0;  // SMs the next Grams leave free
   double* host = nullptr;  // pinned readback buffer
+  int* tmo = nullptr;      // pinned copy of the tensor-core kernels' timeout count
+  int tmo_seen = 0;        // that count when this context last looked
   std::vector<void*> allocs;
   // iteration state
   int iters = 0, matvecs = 0, restarts = 0, last_evals = 0;
@@ -203,6 +205,20 @@ void prof_harvest(gsi_ctx* c) {
     c->pool.push_back(pe.b);
   }
   c->pending.clear();
+}
+
+// After a call's kernels: GSI_ERR_TIMEOUT if a bounded device wait of a
+// tensor-core kernel ran out since the last look (such a kernel drains the
+// tensor core, leaves non-finite outputs and counts the event), else s.
+gsi_status timeout_check(gsi_ctx* c, gsi_status s) {
+  if (!c->tmo) return s;
+  if (oz_timeouts_async(c->tmo, c->st) != GSI_OK || cudaStreamSynchronize(c->st) != cudaSuccess) return s;
+  if (*c->tmo != c->tmo_seen) {
+    c->tmo_seen = *c->tmo;
+    set_last_error("a bounded wait of a tensor-core kernel ran out");
+    return GSI_ERR_TIMEOUT;
+  }
+  return s;
 }
 
 gsi_status readback(gsi_ctx* c, const double* src, int count) {
@@ -689,6 +705,7 @@ gsi_status gsi_destroy(gsi_ctx* c) {
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->host) cudaFreeHost(c->host);
+  if (c->tmo) cudaFreeHost(c->tmo);
   delete c;
   return GSI_OK;
 }
@@ -837,6 +854,10 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       CK(cuda_status_ok(cudaEventCreateWithFlags(&c->ev_e, cudaEventDisableTiming)));
     }
     CK(cuda_status_ok(cudaMallocHost((void**)&c->host, std::max<size_t>(q, 64) * sizeof(double))));
+    CK(cuda_status_ok(cudaMallocHost((void**)&c->tmo, 64)));
+    CK(oz_timeouts_async(c->tmo, c->st));
+    CK(cuda_status_ok(cudaStreamSynchronize(c->st)));
+    c->tmo_seen = *c->tmo;
     if (opts.anorm > 0) {
       c->anorm = opts.anorm;
     } else {
@@ -853,7 +874,7 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       c->anorm = c->host[0];
       if (!(c->anorm > 0)) c->anorm = 1.0;
     }
-    CK(start(c, X0, X0_on_device));
+    CK(timeout_check(c, start(c, X0, X0_on_device)));
   }
 #undef CK
   *out = c;
@@ -865,29 +886,45 @@ fail:
 
 gsi_status gsi_reset(gsi_ctx* c, const double* X0, int32_t X0_on_device) {
   if (!c || !X0) return GSI_ERR_ARG;
-  return start(c, X0, X0_on_device);
+  return timeout_check(c, start(c, X0, X0_on_device));
 }
 
 gsi_status gsi_step(gsi_ctx* c, int32_t nsteps, gsi_info* info) {
   if (!c || nsteps < 0) return GSI_ERR_ARG;
   for (int i = 0; i < nsteps; ++i) {
     bool stop = false;
-    GSI_TRY(c->o.method == GSI_CHEB ? iterate_cheb(c, &stop) : iterate(c, &stop));
+    gsi_status s = c->o.method == GSI_CHEB ? iterate_cheb(c, &stop) : iterate(c, &stop);
+    if (s != GSI_OK) return timeout_check(c, s);
     if (stop) break;
   }
   fill_info(c, info);
-  return GSI_OK;
+  return timeout_check(c, GSI_OK);
 }
 
 gsi_status gsi_solve(gsi_ctx* c, gsi_info* info) {
   if (!c) return GSI_ERR_ARG;
   for (;;) {
     bool stop = false;
-    GSI_TRY(c->o.method == GSI_CHEB ? iterate_cheb(c, &stop) : iterate(c, &stop));
+    gsi_status s = c->o.method == GSI_CHEB ? iterate_cheb(c, &stop) : iterate(c, &stop);
+    if (s != GSI_OK) return timeout_check(c, s);
     if (stop) break;
   }
   fill_info(c, info);
-  return c->converged ? GSI_OK : GSI_ERR_NOCONV;
+  return timeout_check(c, c->converged ? GSI_OK : GSI_ERR_NOCONV);
+}
+
+gsi_status gsi_set_wait_limit(int32_t polls) { return oz_set_wait_limit(polls); }
+
+gsi_status gsi_device_timeouts(int64_t* count) {
+  if (!count) return GSI_ERR_ARG;
+  int* h = nullptr;
+  GSI_CUDA_TRY(cudaMallocHost((void**)&h, sizeof(int)));
+  gsi_status s = oz_timeouts_async(h, 0);
+  cudaError_t e = cudaStreamSynchronize(0);
+  if (s == GSI_OK && e != cudaSuccess) s = cuda_status(e);
+  if (s == GSI_OK) *count = *h;
+  cudaFreeHost(h);
+  return s;
 }
 
 gsi_status gsi_state_ptrs(gsi_ctx* c, void** X, void** Y) {

@@ -129,6 +129,8 @@ def _lib():
             "gsi_restrict": [i32, i32, i32, i32, vp, vp, vp],
             "gsi_gemm_bf16": [i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, ctypes.c_float,
                               ctypes.c_float, vp, vp, i32, vp],
+            "gsi_set_wait_limit": [i32],
+            "gsi_device_timeouts": [ctypes.POINTER(i64)],
             "gsi_profile_enable": [vp, i32],
             "gsi_profile_read": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
                                  ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
@@ -283,6 +285,19 @@ def measure_fma_peaks(stream=None):
     _check(lib().gsi_measure_fma_peaks(ctypes.c_void_p(out.ctypes.data), _stream(stream)),
            "gsi_measure_fma_peaks")
     return {"fp64_fma_tflops": float(out[0]), "fp32_fma_tflops": float(out[1])}
+
+
+def set_wait_limit(polls):
+    """Polls allowed to each bounded wait of the tensor-core kernels on the
+    current device (negative: the default 2^24)."""
+    _check(lib().gsi_set_wait_limit(int(polls)), "gsi_set_wait_limit")
+
+
+def device_timeouts():
+    """Bounded waits that ran out on the current device since the library was loaded."""
+    c = ctypes.c_int64()
+    _check(lib().gsi_device_timeouts(ctypes.byref(c)), "gsi_device_timeouts")
+    return int(c.value)
 
 
 def launch_count():

@@ -23,8 +23,14 @@ def jacobi_eigh(A, sweeps=60, tol=1e-15):
                 aij = A[i, j]
                 if aij == 0.0:
                     continue
-                theta = (A[j, j] - A[i, i]) / (2.0 * aij)
-                t = math.copysign(1.0, theta) / (abs(theta) + math.sqrt(theta * theta + 1.0))
+                d = A[j, j] - A[i, i]
+                if abs(d) > 1e150 * abs(aij):
+                    # theta = d / (2 a_ij) (or theta^2) would overflow; then
+                    # t = 1/(|theta| + sqrt(theta^2 + 1)) = 1/(2 theta) = a_ij / d
+                    t = aij / d
+                else:
+                    theta = d / (2.0 * aij)
+                    t = math.copysign(1.0, theta) / (abs(theta) + math.sqrt(theta * theta + 1.0))
                 c = 1.0 / math.sqrt(t * t + 1.0)
                 s = t * c
                 # A <- J^T A J on rows/columns i, j

@@ -358,3 +358,33 @@ def test_fused_row_norm_matches_separate_pass(torch_cuda):
     assert abs(a["rel_residual"] - b["rel_residual"]) <= 1e-4 * b["rel_residual"]
     assert np.isfinite(a["rel_residual_inf"]) and a["rel_residual_inf"] > 0
     assert abs(a["rel_residual_inf"] - b["rel_residual_inf"]) <= 1e-3 * b["rel_residual_inf"]
+
+
+@pytest.mark.parametrize("dims,p,precision", [((32, 32), 8, "df64"), ((32, 32), 7, "df64"),
+                                              ((32, 32), 8, "f64"), ((16, 16, 16), 64, "df64")])
+def test_residual_inf_matches_oracle(torch_cuda, dims, p, precision):
+    """The paper's table criterion ||R_k||_inf / ||R_0||_inf (largest row sum of
+    |R|, Table "Comparison of LOBCG and Riemannian CG") over the first 10 CG
+    iterations, against the oracle's record from the same start. df64: the row
+    sums are float32 sums of the high words -- formed in the tcgen05 block
+    product's epilogue for even p <= 64 (a 6-level tree per row), in a separate
+    reduction otherwise (p - 1 sequential adds) -- so each norm is within
+    (p + 1) 2^-24 relative of the exact one and the ratio within twice that.
+    float64: a float64 reduction, 1e-12. Both plus the trajectory's own drift
+    (iterates within 1e-10 of the oracle's), 1e-9 absolute."""
+    from paper_2306_10379_gb300 import gsi
+    A = I.fd_laplacian(dims)
+    S = O.csr_operator(A.n, A.rowptr, A.colidx, A.val)
+    lam = I.laplacian_eigenvalues(dims)
+    X0 = I.start_block(A.n, p, I.SEED_BASE)
+    hist = O.solve(S, X0, O.Options(method="cg", tol=1e-8, anorm=lam[0], max_iters=10), record=True).history
+    assert len(hist) == 10
+    rel = 2.0 * (p + 1) * 2.0 ** -24 if precision == "df64" else 1e-12
+    worst = 0.0
+    with gsi.Solver(A, p, X0, method="cg", tol=1e-8, anorm=lam[0], precision=precision) as s:
+        for k in range(10):
+            got = s.step(1)["rel_residual_inf"]
+            want = hist[k].res_inf
+            assert abs(got - want) <= rel * want + 1e-9, (k, got, want)
+            worst = max(worst, abs(got - want) / want)
+    assert hist[-1].res_inf < hist[0].res_inf  # the criterion moved over the 10 steps

@@ -1,4 +1,4 @@
-"""Pins of the oracle's LOBCG comparator (Sec. 7, comparison to LOBCG) against
+"""Pins of the oracle's LOBCG comparator (Sec. 6.4, comparison to LOBCG) against
 facts that do not depend on it: App. A's containment of the Riemannian CG
 iterate in the LOBCG subspace and the resulting bound on phi, the p = 1 case
 (one Rayleigh-Ritz step on span(x, g) is the exact steepest-descent step),
