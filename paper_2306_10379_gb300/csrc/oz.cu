@@ -728,6 +728,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     // core (bounded), poison this block's rows so the caller sees non-finite
     // values, and release the tensor memory
     if (tid == 0) atomicAdd(&g_oz_tc_timeouts, 1);
+    tc_wait(mb, phase ^ 1u, TC_WAIT_LIMIT);  // the tile's one pending commit
     tc_drain(issuer && lane == 0, smem_addr(mbar + 1));
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
       for (int e = tid; e < TC_M * NC; e += TC_THREADS) {
@@ -1126,12 +1127,11 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
     for (int s = 0; s < NSUB; ++s) {
       const int buf = s & 1;
       bool ok = true;
-      if (s >= 2) {  // the products of sub-chunk s - 2 read this buffer
-        if (!issuer) ok = tc_wait(buf ? mb1 : mb0, buf ? ph1 : ph0, wait_limit);
-        if (buf) ph1 ^= 1u;
-        else ph0 ^= 1u;
-      }
-      if (!issuer) {
+      // the products of sub-chunk s - 2 read this buffer; the phase bit moves
+      // on only once every thread saw them complete, so that after a wait
+      // that ran out ph0 / ph1 still name each barrier's pending commit
+      if (s >= 2 && !issuer) ok = tc_wait(buf ? mb1 : mb0, buf ? ph1 : ph0, wait_limit);
+      if (!issuer && ok) {
         unsigned char* dst = dig + buf * TG_DBUF + (isv ? 7 * plane : 0);
         const int r = irow + s * SK;
         const int E = (isv ? Ev : Eu)[ic];
@@ -1151,6 +1151,10 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
+      }
+      if (s >= 2) {
+        if (buf) ph1 ^= 1u;
+        else ph0 ^= 1u;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (issuer) {
@@ -1182,12 +1186,12 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
       ok = tc_wait(mb0, ph0, wait_limit);
       ok = tc_wait(mb1, ph1, wait_limit) && ok;
     }
-    ph0 ^= 1u;
-    ph1 ^= 1u;
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
+    ph0 ^= 1u;
+    ph1 ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!issuer) {
       const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
@@ -1218,8 +1222,14 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   if (!issuer) cp_async_wait_all();
   if (failed) {
     // a product that did not complete in time: count it, drain the tensor
-    // core (bounded), and report non-finite partial sums
+    // core (bounded), and report non-finite partial sums. Each barrier has
+    // exactly one pending commit here (sub-chunks s - 2 and s - 1, or the
+    // chunk's last two), named by ph0 / ph1; waiting for both lets their
+    // arrivals land before the block exits, and the final commit covers
+    // anything else issued.
     if (tid == 0) atomicAdd(&g_oz_tc_timeouts, 1);
+    tc_wait(mb0, ph0, TC_WAIT_LIMIT);
+    tc_wait(mb1, ph1, TC_WAIT_LIMIT);
     tc_drain(issuer && lane == 0, smem_addr(mbar + 2));
 #pragma unroll
     for (int e = 0; e < 16; ++e) res[e] = make_float2(NAN, NAN);
