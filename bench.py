@@ -26,26 +26,29 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Iterations this workload needs to reach the tolerance (start block seed
-# SEED_BASE + 1); the oracle follows the same iteration (trajectory parity),
-# so the reference arm scales its per-iteration time by it.
-ITERS_TO_TOL = {"cg": 4953, "sd": None}
-WARMUP_ITERS = 200
+WARMUP_ITERS = 200     # a warm-up step: a solve capped at this many iterations
+F64_TIMED_ITERS = 200  # event-timed iterations of the native float64 baseline
+# Iterations the library's CG solve of the default workload (128^3, p = 64,
+# start block SEED_BASE + 1) takes to 1e-8, as measured by this script's
+# default line; the reference arm (a separate process, the oracle alone)
+# scales its time per iteration by it. The oracle follows the same
+# trajectory: whole-solve iteration counts agree within 2% in the parity
+# tests, up to the 3D sizes the oracle finishes there. A full oracle run at
+# this size (~5,000 iterations at several seconds each) is out of reach.
+GPU_ITERS_TO_TOL = {("cg", 128, 64): 4953}
 
-# DRAM bytes per launch from one ncu capture of the kernel (profiles/), scaled
-# to the bench size by the rows processed (traffic grows in proportion).
+# DRAM read + write bytes per launch from one-kernel ncu captures at
+# n = 512,000 (80^3), p = 64, scaled to the bench size by the rows processed
+# (traffic grows in proportion); averaged over one iteration's launches of the
+# class (2 U^T U + 3 U^T V Grams; 2 fused retractions + 2 products with
+# elementwise terms). None where the kernel changed after the capture.
 NCU_TRAFFIC = {
-    # DRAM read + write per launch at n = 512,000, p = 64 (profiles/digit_kernels_fd3d80_p64.md),
-    # averaged over one iteration's launches of the class (2 U^T U + 3 U^T V Grams; 2 fused
-    # retractions + 2 products with elementwise terms, R's counters standing for D's)
     "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.249e6 + 3.685e6) + 3 * (524.391e6 + 3.592e6)) / 5},
     "blockmul": {"n": 512000, "p": 64, "bytes": ((524.523e6 + 226.326e6) + (524.506e6 + 226.865e6)
                                                   + 2 * (786.842e6 + 240.490e6)) / 4},
-    "spmm": {"n": 512000, "p": 64, "bytes": 308.8e6 + 229.4e6},
+    "spmm": None,
 }
-
-
-FP64_FMA_TFLOPS = 1.25  # measured float64 FMA throughput of this GPU (profiles/fma_peaks_gb300.md)
+TRAFFIC_SOURCE = "one-kernel ncu captures at 80^3 (n = 512,000, p = 64), scaled by rows"
 
 
 def _class_entry(v):
@@ -67,14 +70,20 @@ def parse():
     ap.add_argument("--fmt", default="csr", choices=["csr", "sell"])
     ap.add_argument("--precision", default="df64", choices=["df64", "f64"])
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=25.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the native float64 baseline")
+    ap.add_argument("--no-forms", action="store_true", help="skip the dense and batched forms")
     ap.add_argument("--workload", default="fd3d", choices=["fd3d", "dense", "batched", "warm"],
-                    help="fd3d (default): the 128^3 plain solve; dense: mixed precision against "
-                         "float64 on a dense n = 16384, p = 128 spectrum; batched: 512 Erdos-Renyi "
-                         "problems in one graph launch against the plain solver one problem at a "
-                         "time; warm: learned against random start on a diffusion family")
+                    help="fd3d (default): the 128^3 plain solve with the float64 baseline and the "
+                         "forms; dense: mixed precision against float64 on a dense n = 16384, "
+                         "p = 128 spectrum; batched: 512 Erdos-Renyi problems in one graph launch "
+                         "against the plain solver one problem at a time; warm: learned against "
+                         "random start on a diffusion family")
+    # internal: one CPU-oracle sample in a child process with a thread cap
+    ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--threads", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -153,7 +162,7 @@ class ClockSampler:
 
 def cpu_oracle_sample(args, A, lam, X0, seconds):
     """Time the float64 oracle's iteration on the full workload for a bounded
-    number of iterations; returns (seconds per iteration, iterations, threads)."""
+    number of iterations; returns (seconds per iteration, iterations)."""
     from oracle import gsi_oracle as O
     S = O.csr_operator(A.n, A.rowptr, A.colidx, A.val)
     times = []
@@ -174,34 +183,65 @@ def cpu_oracle_sample(args, A, lam, X0, seconds):
         pass
     # the first interval includes the start-block orthonormalisation and AX
     per_it = sum(times[1:]) / max(1, len(times) - 1) if len(times) > 1 else times[0]
-    return per_it, len(times), os.cpu_count()
+    return per_it, len(times)
+
+
+def cpu_child(args):
+    """--cpu-child X0.npy: one oracle sample in this process (started with its
+    BLAS thread cap in the environment); prints a JSON line."""
+    import numpy as np
+    from paper_2306_10379_gb300 import inputs as I
+    g = args.grid
+    A = I.fd_laplacian((g, g, g))
+    lam = I.laplacian_eigenvalues((g, g, g))
+    X0 = np.load(args.cpu_child, mmap_mode="r")
+    per_it, n_it = cpu_oracle_sample(args, A, lam, np.ascontiguousarray(X0), args.cpu_seconds)
+    print(json.dumps({"per_it": per_it, "n_it": n_it, "threads": args.threads}), flush=True)
+    return 0
+
+
+def cpu_oracle_threads(args, x0_path, threads):
+    """The oracle sample in a child process whose BLAS thread pools are capped
+    at `threads` (the sparse product is single-threaded either way)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", x0_path, "--threads", str(threads),
+           "--grid", str(args.grid), "--method", args.method, "--cpu-seconds", str(args.cpu_seconds)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    for ln in r.stdout.splitlines()[::-1]:
+        if ln.startswith("{"):
+            return json.loads(ln)
+    raise RuntimeError("CPU oracle sample failed: " + r.stderr[-500:])
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    A, lam, X0 = workload(args)
-    its = ITERS_TO_TOL.get(args.method)
+    its = GPU_ITERS_TO_TOL.get((args.method, args.grid, args.p)) if args.tol == 1e-8 else None
     if its is None:
-        print(json.dumps({"impl": "reference", "unavailable": "no iteration count recorded for this method"}))
+        print(json.dumps({"impl": "reference", "unavailable": "no recorded iteration count for this workload"}))
         return 0
+    A, lam, X0 = workload(args)
     steps_ms = []
-    per_it = n_it = threads = None
+    per_it = n_it = None
     for i in range(args.warmup + args.steps):
-        per_it, n_it, threads = cpu_oracle_sample(args, A, lam, X0, args.cpu_seconds)
+        per_it, n_it = cpu_oracle_sample(args, A, lam, X0, args.cpu_seconds)
         if i >= args.warmup:
             steps_ms.append(per_it * its * 1e3)
     value = sum(steps_ms) / len(steps_ms)
     sample = (f"{n_it} iterations of the float64 numpy/scipy oracle on the full workload "
-              f"(~{args.cpu_seconds:g} s per step), time per iteration x {its} iterations to tolerance")
+              f"(~{args.cpu_seconds:g} s per step), time per iteration x {its} iterations to tolerance "
+              f"(the library's solve of the same start block; the oracle follows the same trajectory)")
     out = {
         "metric": metric_name(), "value": value, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": workload_name(args, A.n), "p": args.p, "n": A.n},
-        "cpu_baseline": {"value": value, "unit": "ms", "cores": threads, "kind": "oracle",
+        "config": {"workload": workload_name(args, A.n), "p": args.p, "n": A.n, "iterations": its},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -209,12 +249,138 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# The precision, batching and warm-start forms against the plain GPU solve of
+# the same problems. form_dense / form_batched return a dict (the default
+# line's "forms"); --workload dense|batched|warm prints each as its own line.
+# ---------------------------------------------------------------------------
 
-# ---------------------------------------------------------------------------
-# Further workloads (not the default line): the precision, batching and
-# warm-start forms against the plain float64-class GPU solve of the same
-# problems. Each prints one JSON line with the comparison in "baseline".
-# ---------------------------------------------------------------------------
+def form_dense(args, reps=3):
+    """Dense A = Q diag(lam) Q^T (n = 16384, p = 128, gap 1e-2 above the rest of
+    the spectrum): the mixed-precision solve (3-digit direction apply, 7-digit
+    correction phase) against the float64 and df64 solves of the same problem.
+    Returns (result dict, clocks, launches)."""
+    import numpy as np
+    import torch
+    from paper_2306_10379_gb300 import gsi, inputs as I
+    n, p = 16384, 128
+    A, lam = I.dense_spectrum(n, p, 1e-2, I.SEED_BASE + 3)
+    X0 = torch.from_numpy(I.start_block(n, p, I.SEED_BASE + 3)).cuda()
+    Ad = gsi.Dense(torch.from_numpy(A).cuda())
+    res = {}
+    clk = launches = None
+    for prec in ("mixed", "df64", "f64"):
+        s = gsi.Solver(Ad, p, X0, method="cg", tol=1e-8, anorm=float(lam[0]), precision=prec)
+        r = reps if prec == "mixed" else 1
+        if prec == "mixed":
+            for _ in range(max(1, args.warmup)):
+                s.reset(X0)
+                s.step(20)
+            clocks = ClockSampler(0)
+            clocks.start()
+            l0 = gsi.launch_count()
+        ms, info = _timed(torch, lambda: (s.reset(X0), s.solve())[1], r)
+        if prec == "mixed":
+            clk = clocks.stop()
+            launches = gsi.launch_count() - l0
+        _, ev = s.basis()
+        res[prec] = {"ms": ms, "iters": info["iters"], "matvecs": info["matvecs"],
+                     "rel_residual": info["rel_residual"],
+                     "ritz_max_abs_err": float(np.max(np.abs(ev - lam[:p])))}
+        s.close()
+    m = res["mixed"]
+    out = {"workload": "dense A = Q diag(lam) Q^T, n=16384, p=128 largest, gap 1e-2, RCG, rel. residual 1e-8",
+           "mixed_ms": m["ms"], "mixed": m, "plain_f64_gpu": res["f64"], "df64_gpu": res["df64"],
+           "speedup_vs_f64": res["f64"]["ms"] / m["ms"], "speedup_vs_df64": res["df64"]["ms"] / m["ms"],
+           "error_vs_fp64": "Ritz values against the prescribed spectrum (ritz_max_abs_err per form)"}
+    return out, clk, launches
+
+
+def form_batched(args, sample=64):
+    """512 Erdos-Renyi graph Laplacians (mean degree 8, diagonal shift U(0,1),
+    n_i ~ U[2048, 65536], p_i ~ U{4, 8, 16, 32}), dominant p_i-dimensional
+    subspaces by CG to 1e-8 in one while-graph launch, against the plain
+    solver run one problem after another on every (512/sample)-th problem.
+    Returns (result dict, clocks, launches)."""
+    import numpy as np
+    import torch
+    from paper_2306_10379_gb300 import gsi, inputs as I
+    t0 = time.time()
+    B = I.er_batch(512, I.SEED_BASE + 4)
+    gen_s = time.time() - t0
+    b = gsi.Batch(B, method="cg", tol=1e-8, max_iters=5000)
+    tuned = b.tune(3)
+    for _ in range(max(1, args.warmup)):  # warm-up: the same passes, capped
+        b.reset()
+        b.step(30)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = gsi.launch_count()
+    times = []
+    passes = None
+    for _ in range(max(1, min(args.steps, 3))):
+        b.reset()
+        ms, passes = _timed(torch, lambda: b.solve(use_graph=True, check=False), 1)
+        times.append(ms)
+    clk = clocks.stop()
+    launches = gsi.launch_count() - l0
+    infos = [b.info(i) for i in range(B.nprob)]
+    b.close()
+    its = np.array([f["iters"] for f in infos])
+    conv = int(sum(f["converged"] for f in infos))
+    stride = B.nprob // sample
+    idx = list(range(0, B.nprob, stride))[:sample]
+    plain_ms = 0.0
+    plain_its = []
+    for i in idx:
+        s = gsi.Solver(B.mats[i], int(B.p[i]), B.X0s[i], method="cg", tol=1e-8, max_iters=5000)
+        ms, info = _timed(torch, lambda: s.solve(), 1)
+        s.close()
+        plain_ms += ms
+        plain_its.append(info["iters"])
+    est = plain_ms / len(idx) * B.nprob
+    value = float(np.mean(times))
+    out = {"workload": "512 Erdos-Renyi graph Laplacians + diag U(0,1), n_i in [2048, 65536], "
+                       "p_i in {4,8,16,32}, RCG, rel. residual 1e-8, one while-graph launch",
+           "batched_ms": value, "problems": B.nprob, "sum_n": int(B.n.sum()),
+           "sum_np": int((B.n.astype(np.int64) * B.p).sum()), "passes": passes, "converged": conv,
+           "iters_max": int(its.max()), "iters_mean": float(its.mean()), "tiles": tuned,
+           "generation_s": gen_s,
+           "plain_one_at_a_time_ms_est": est,
+           "plain_sample": f"{len(idx)} problems (every {stride}th) solved one after another with gsi_solve "
+                           f"in {plain_ms:.0f} ms (mean {np.mean(plain_its):.0f} iterations), scaled by "
+                           f"{B.nprob}/{len(idx)}",
+           "speedup": est / value}
+    return out, clk, launches
+
+
+def run_dense(args):
+    import torch  # noqa: F401
+    from paper_2306_10379_gb300 import build
+    build.build()
+    d, clk, launches = form_dense(args, reps=max(1, args.steps))
+    _line(args, "ms to rel. residual 1e-8 (mixed precision vs float64 GPU)", d["mixed_ms"],
+          {"workload": d["workload"], "n": 16384, "p": 128,
+           "precision": "mixed (3-digit apply, 7-digit correction)", "iterations": d["mixed"]["iters"],
+           "rel_residual": d["mixed"]["rel_residual"], "ritz_max_abs_err": d["mixed"]["ritz_max_abs_err"]},
+          "bf16 tensor-core digits (3 then 7 per operand), df64 blocks, f64 p x p",
+          {"baseline": {"plain_f64_gpu": d["plain_f64_gpu"], "df64_gpu": d["df64_gpu"],
+                        "speedup_vs_f64": d["speedup_vs_f64"]},
+           "clocks": clk, "gpu_launches": launches})
+
+
+def run_batched(args):
+    from paper_2306_10379_gb300 import build
+    build.build()
+    d, clk, launches = form_batched(args)
+    cfg = {k: v for k, v in d.items() if k not in ("batched_ms", "plain_one_at_a_time_ms_est",
+                                                   "plain_sample", "speedup")}
+    _line(args, "ms to rel. residual 1e-8 (batched vs one-at-a-time GPU)", d["batched_ms"], cfg,
+          "df64 blocks (float32 pairs), float32 operator entries, df64 p x p step",
+          {"baseline": {"plain_one_at_a_time_ms_est": d["plain_one_at_a_time_ms_est"],
+                        "sample": d["plain_sample"], "speedup": d["speedup"]},
+           "clocks": clk, "gpu_launches": launches})
+
 
 def _line(args, metric, value, cfg, dtype, extra):
     out = {"metric": metric, "value": value, "unit": "ms", "n_gpus": 1, "steps": args.steps,
@@ -232,106 +398,6 @@ def _timed(torch, fn, steps):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps, res[-1]
-
-
-def run_dense(args):
-    """Dense A = Q diag(lam) Q^T (n = 16384, p = 128, gap 1e-2 above the rest of
-    the spectrum): the mixed-precision solve (3-digit direction apply, 7-digit
-    correction phase) against the float64 and df64 solves of the same problem."""
-    import numpy as np
-    import torch
-    from paper_2306_10379_gb300 import build, gsi, inputs as I
-    build.build()
-    n, p = 16384, 128
-    A, lam = I.dense_spectrum(n, p, 1e-2, I.SEED_BASE + 3)
-    X0 = torch.from_numpy(I.start_block(n, p, I.SEED_BASE + 3)).cuda()
-    Ad = gsi.Dense(torch.from_numpy(A).cuda())
-    res = {}
-    for prec in ("mixed", "df64", "f64"):
-        s = gsi.Solver(Ad, p, X0, method="cg", tol=1e-8, anorm=float(lam[0]), precision=prec)
-        reps = args.steps if prec == "mixed" else 1
-        if prec == "mixed":
-            for _ in range(args.warmup):
-                s.reset(X0)
-                s.step(20)
-            clocks = ClockSampler(0)
-            clocks.start()
-            l0 = gsi.launch_count()
-        ms, info = _timed(torch, lambda: (s.reset(X0), s.solve())[1], reps)
-        if prec == "mixed":
-            clk = clocks.stop()
-            launches = gsi.launch_count() - l0
-        _, ev = s.basis()
-        res[prec] = {"ms": ms, "iters": info["iters"], "rel_residual": info["rel_residual"],
-                     "ritz_max_abs_err": float(np.max(np.abs(ev - lam[:p])))}
-        s.close()
-    m = res["mixed"]
-    _line(args, "ms to rel. residual 1e-8 (mixed precision vs float64 GPU)", m["ms"],
-          {"workload": "dense A = Q diag(lam) Q^T, n=16384, p=128 largest, gap 1e-2, RCG, rel. residual 1e-8",
-           "n": n, "p": p, "precision": "mixed (3-digit apply, 7-digit correction)", "iterations": m["iters"],
-           "rel_residual": m["rel_residual"], "ritz_max_abs_err": m["ritz_max_abs_err"]},
-          "bf16 tensor-core digits (3 then 7 per operand), df64 blocks, f64 p x p",
-          {"baseline": {"plain_f64_gpu": res["f64"], "df64_gpu": res["df64"],
-                        "speedup_vs_f64": res["f64"]["ms"] / m["ms"]},
-           "clocks": clk, "gpu_launches": launches})
-
-
-def run_batched(args):
-    """512 Erdos-Renyi graph Laplacians (mean degree 8, diagonal shift U(0,1),
-    n_i ~ U[2048, 65536], p_i ~ U{4, 8, 16, 32}), dominant p_i-dimensional
-    subspaces by CG to 1e-8 in one while-graph launch, against the plain
-    solver run one problem after another on a sample of the same problems."""
-    import numpy as np
-    import torch
-    from paper_2306_10379_gb300 import build, gsi, inputs as I
-    build.build()
-    t0 = time.time()
-    B = I.er_batch(512, I.SEED_BASE + 4)
-    gen_s = time.time() - t0
-    b = gsi.Batch(B, method="cg", tol=1e-8, max_iters=5000)
-    tuned = b.tune(3)
-    for _ in range(args.warmup):  # warm-up: the same passes, capped
-        b.reset()
-        b.step(30)
-    clocks = ClockSampler(0)
-    clocks.start()
-    l0 = gsi.launch_count()
-    times = []
-    for _ in range(args.steps):
-        b.reset()
-        ms, passes = _timed(torch, lambda: b.solve(use_graph=True, check=False), 1)
-        times.append(ms)
-    clk = clocks.stop()
-    launches = gsi.launch_count() - l0
-    infos = [b.info(i) for i in range(B.nprob)]
-    b.close()
-    its = np.array([f["iters"] for f in infos])
-    conv = int(sum(f["converged"] for f in infos))
-    # the plain solver, one problem at a time, on the first 6 problems
-    sample = 6
-    plain_ms = 0.0
-    plain_its = []
-    for i in range(sample):
-        m = B.mats[i]
-        s = gsi.Solver(m, int(B.p[i]), B.X0s[i], method="cg", tol=1e-8, max_iters=5000)
-        ms, info = _timed(torch, lambda: s.solve(), 1)
-        s.close()
-        plain_ms += ms
-        plain_its.append(info["iters"])
-    est = plain_ms / sample * B.nprob
-    value = float(np.mean(times))
-    _line(args, "ms to rel. residual 1e-8 (batched vs one-at-a-time GPU)", value,
-          {"workload": "512 Erdos-Renyi graph Laplacians + diag U(0,1), n_i in [2048, 65536], "
-                       "p_i in {4,8,16,32}, RCG, rel. residual 1e-8, one while-graph launch",
-           "problems": B.nprob, "sum_n": int(B.n.sum()), "sum_np": int((B.n.astype(np.int64) * B.p).sum()),
-           "passes": passes, "converged": conv, "iters_max": int(its.max()), "iters_mean": float(its.mean()),
-           "tiles": tuned, "generation_s": gen_s},
-          "df64 blocks (float32 pairs), float32 operator entries, df64 p x p step",
-          {"baseline": {"plain_one_at_a_time_ms_est": est,
-                        "sample": f"{sample} problems solved one after another with gsi_solve "
-                                  f"({plain_ms:.0f} ms, iterations {plain_its}), scaled by {B.nprob}/{sample}",
-                        "speedup": est / value},
-           "clocks": clk, "gpu_launches": launches})
 
 
 def run_warm(args):
@@ -426,12 +492,43 @@ def run_warm(args):
                         "speedup": ms_random / value},
            "clocks": clk, "gpu_launches": launches})
 
+def f64_baseline(args, Ad, X0d, lam, iters_to_tol):
+    """Native float64 GPU solve of the same workload: F64_TIMED_ITERS
+    iterations timed with events after a short warm-up, and the time to
+    tolerance extrapolated with the df64 solve's iteration count (the two
+    follow the oracle's trajectory)."""
+    import torch
+    from paper_2306_10379_gb300 import gsi
+    s = gsi.Solver(Ad, args.p, X0d, method=args.method, tol=args.tol, anorm=float(lam[0]), fmt=args.fmt,
+                   precision="f64")
+    s.step(3)
+    s.profile(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    info = s.step(F64_TIMED_ITERS)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.close()
+    done = info["iters"] - 3
+    ms_it = e0.elapsed_time(e1) / max(1, done)
+    return {"precision": "f64 (native float64 pipe)", "iterations_timed": done, "ms_per_iteration": ms_it,
+            "est_ms_to_tol": ms_it * iters_to_tol,
+            "kind": f"extrapolated: event-timed ms per iteration x {iters_to_tol} iterations (the df64 solve's "
+                    f"count; both follow the oracle's trajectory)",
+            "classes": {k: _class_entry(v) for k, v in prof.items() if v["launches"]}}
+
+
 def main():
     args = parse()
+    if args.cpu_child:
+        return cpu_child(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "fd3d":
         return {"dense": run_dense, "batched": run_batched, "warm": run_warm}[args.workload](args)
+    import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -451,12 +548,21 @@ def main():
         dist.barrier()
     A, lam, X0 = workload(args)
     n, p = A.n, args.p
+    solo = rank == 0 and world == 1
 
-    # CPU baseline first (before device work), rank 0 at N=1 only
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        per_it, n_it, threads = cpu_oracle_sample(args, A, lam, X0, args.cpu_seconds)
-        cpu = (per_it, n_it, threads)
+    # CPU baselines first (before device work), rank 0 at N=1 only: the
+    # oracle with all host cores and with one, each in a child process
+    cpu = {}
+    if solo and not args.no_cpu:
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "x0.npy")
+            np.save(path, X0)
+            for th in (os.cpu_count(), 1):
+                try:
+                    cpu[th] = cpu_oracle_threads(args, path, th)
+                except Exception as e:  # reported, not fatal
+                    cpu[th] = {"error": str(e)[-300:]}
 
     stream = torch.cuda.current_stream()
 
@@ -469,6 +575,7 @@ def main():
     Ad.colidx = torch.from_numpy(A.colidx).cuda()
     Ad.val = torch.from_numpy(A.val).cuda()
     X0d = torch.from_numpy(X0).cuda()
+    fma = gsi.measure_fma_peaks()
     s = gsi.Solver(Ad, p, X0d, method=args.method, tol=args.tol, anorm=float(lam[0]), fmt=args.fmt,
                    precision=args.precision)
     info = None
@@ -506,9 +613,15 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     info = infos[-1]
-    # accuracy of the result (explicit residual with the Ritz pair, float64)
+    # accuracy of the result against float64: Ritz values against the closed
+    # form, and the explicit float64 residual of the Ritz pairs
     Xr, ev = s.basis()
     s.close()
+    Xr = np.asarray(Xr)
+    import scipy.sparse as sp_
+    Rr = sp_.csr_matrix((A.val, A.colidx, A.rowptr), shape=(n, n)) @ Xr - Xr * ev
+    res_f64 = float(np.linalg.norm(Rr) / lam[0])
+    del Rr, Xr
 
     # dominant kernel class and its roofline
     peaks = {}
@@ -518,25 +631,26 @@ def main():
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s (of fallback)"
+
+    def traffic_of(k):
+        tr = NCU_TRAFFIC.get(k)
+        return tr["bytes"] * n / tr["n"] if tr is not None and tr["p"] == p else None
+
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     avg_ms = d["ms"] / max(1, d["launches"])
     bytes_per = d["bytes"] / max(1, d["launches"])
     achieved = bytes_per / (avg_ms * 1e-3) / 1e9
-    traffic = None
-    tr = NCU_TRAFFIC.get(dom)
-    if tr is not None and tr["p"] == p:
-        traffic = tr["bytes"] * n / tr["n"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic, "kernel": dom,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
-                else "fallback 6.8 TB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic_of(dom), "traffic_source": TRAFFIC_SOURCE,
+                "kernel": dom, "peak_source": peak_src,
                 "launch_ms": avg_ms, "alg_bytes_per_launch": bytes_per,
                 "classes": {k: _class_entry(v) for k, v in prof.items()},
                 # the digit-product classes run float64-class products; their rate in
                 # float64 flops (2 n p^2 per Gram, 2 n p^2 nk per block product) next to
-                # the measured float64 FMA peak (profiles/fma_peaks_gb300.md)
-                "fp64_fma_peak_tflops": FP64_FMA_TFLOPS}
+                # this GPU's float64 FMA throughput measured in this run
+                "fp64_fma_peak_tflops": fma["fp64_fma_tflops"], "fp32_fma_peak_tflops": fma["fp32_fma_tflops"]}
 
     # the block matvec (SpMM) against the HBM roofline
     sp = prof.get("spmm", {"launches": 0})
@@ -546,30 +660,33 @@ def main():
         sp_b = sp["bytes"] / sp["launches"]
         spmm_roofline = {"bound": "hbm", "achieved": sp_b / (sp_ms * 1e-3) / 1e9, "peak": hbm_peak,
                          "unit": "GB/s", "frac": sp_b / (sp_ms * 1e-3) / 1e9 / hbm_peak,
-                         "launch_ms": sp_ms, "alg_bytes_per_launch": sp_b,
-                         "traffic": (NCU_TRAFFIC["spmm"]["bytes"] * n / NCU_TRAFFIC["spmm"]["n"]
-                                     if p == NCU_TRAFFIC["spmm"]["p"] else None)}
+                         "launch_ms": sp_ms, "alg_bytes_per_launch": sp_b, "traffic": traffic_of("spmm")}
     out = {
         "metric": metric_name(), "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "warmup_kind": f"solves capped at {WARMUP_ITERS} iterations (same kernels and shapes)",
-        "vs_baseline": None, "dtype": "df64 (fp32 pairs) + bf16 tensor-core digit products; f64 p x p"
+        "vs_baseline": None,
+        "dtype": ("df64: float32 pairs (48-bit significand, float32 exponent range) with bf16 tensor-core "
+                  "digit products exact to 2^-45 of the row/column scale; f64 p x p step. The library's "
+                  "float64-class precision form; the native float64 solve is in 'baseline'")
         if args.precision == "df64" else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, n), "n": n, "p": p, "nnz": int(A.nnz),
                    "method": args.method, "format": args.fmt, "precision": args.precision,
                    "l2": "working set ~10 GB >> 129 MB L2, no flush needed",
                    "iterations": info["iters"], "matvecs": info["matvecs"],
                    "rel_residual": info["rel_residual"],
-                   "ritz_max_rel_err": float(max(abs(ev - lam[:p]) / lam[:p]))},
+                   "error_vs_fp64": {
+                       "ritz_max_rel_err_vs_closed_form": float(max(abs(ev - lam[:p]) / lam[:p])),
+                       "rel_residual_explicit_f64": res_f64,
+                       "how": "Ritz values of the returned basis against the closed-form spectrum; "
+                              "||A X - X diag(theta)||_F / lambda_1 in float64 on the host"}},
         "roofline": roofline,
         "spmm_roofline": spmm_roofline,
         "clocks": clk,
         "gpu_launches": launches,
     }
-
-    if rank == 0 and world == 1 and not args.no_e2e:
+    if solo and not args.no_e2e:
         # end to end through the public API from pinned host buffers
-        import numpy as np
         pin = lambda a: torch.from_numpy(a).pin_memory()
         hp = [pin(A.rowptr), pin(A.colidx), pin(A.val), pin(X0)]
 
@@ -595,12 +712,37 @@ def main():
         h2d = A.rowptr.nbytes + A.colidx.nbytes + A.val.nbytes + X0.nbytes
         out["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(Xout.nbytes + evh.nbytes)}
-    if cpu is not None:
-        per_it, n_it, threads = cpu
-        out["cpu_baseline"] = {
-            "value": per_it * info["iters"] * 1e3, "unit": "ms", "cores": threads, "kind": "oracle",
-            "sample": f"{n_it} iterations of the float64 numpy/scipy oracle on the full workload "
-                      f"({args.cpu_seconds:g} s), time per iteration x {info['iters']} GPU iterations"}
+    if solo and not args.no_baseline and args.precision == "df64":
+        b = f64_baseline(args, Ad, X0d, lam, info["iters"])
+        b["speedup_df64_vs_f64"] = b["est_ms_to_tol"] / ms
+        out["baseline"] = {"plain_f64_gpu": b}
+    if solo and not args.no_forms:
+        del Ad, X0d
+        torch.cuda.empty_cache()
+        forms = {}
+        for name, fn in (("dense_mixed", form_dense), ("batched", form_batched)):
+            try:
+                forms[name] = fn(args)[0]
+            except Exception as e:  # reported, not fatal to the headline line
+                forms[name] = {"error": str(e)[-300:]}
+        out["forms"] = forms
+    if cpu:
+        entries = {}
+        for th, r in cpu.items():
+            if "per_it" in r:
+                entries[th] = {
+                    "value": r["per_it"] * info["iters"] * 1e3, "unit": "ms", "cores": th, "kind": "oracle",
+                    "sample": f"{r['n_it']} iterations of the float64 numpy/scipy oracle on the full workload "
+                              f"({args.cpu_seconds:g} s, BLAS threads capped at {th}; the sparse product is "
+                              f"single-threaded), time per iteration x {info['iters']} iterations (this run's "
+                              f"GPU count; the oracle follows the same trajectory)"}
+            else:
+                entries[th] = {"cores": th, "error": r.get("error")}
+        allc = entries.get(os.cpu_count())
+        if allc is not None and "value" in allc:
+            out["cpu_baseline"] = dict(allc)
+            if 1 in entries and os.cpu_count() != 1:
+                out["cpu_baseline"]["one_core"] = entries[1]
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

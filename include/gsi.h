@@ -150,6 +150,19 @@ gsi_status gsi_get_basis(gsi_ctx* ctx, double* X, double* evals, int32_t to_devi
  * reusing the context's device memory (X0 as in gsi_create). */
 gsi_status gsi_reset(gsi_ctx* ctx, const double* X0, int32_t X0_on_device);
 
+/* Subspace tracking (Sec. 1: eigenspaces of a slowly varying matrix, as in
+ * self-consistent-field iterations). Replaces the context's operator by A --
+ * same format and n as at gsi_create; nnz may change (the buffers are
+ * reallocated) -- and makes the current iterate X the start block of the new
+ * problem: X is orthonormalised again, Y = A X is formed, the iteration
+ * counters and the CG state (direction, previous residual) start afresh.
+ * anorm > 0 sets the bound of the stopping test; otherwise the one given in
+ * gsi_create's options is kept, or ||A||_inf of the new A is used if none
+ * was given. A is copied as in gsi_create (host or device arrays by
+ * A->on_device; the caller keeps them). GSI_ERR_ARG if the format or n
+ * differ. */
+gsi_status gsi_set_operator(gsi_ctx* ctx, const gsi_matrix* A, double anorm);
+
 /* Device pointers of the context's current iterate X and Y = AX (n x p
  * row-major; float64 for GSI_PREC_F64, df64 pairs for GSI_PREC_DF64), valid
  * until the next call on ctx. For tests and benchmarks. */

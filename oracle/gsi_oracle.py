@@ -36,7 +36,11 @@ Readings of points the paper leaves open:
   * LOBCG (the comparator of Sec. 6.4): the basis of span(X_k, G_k, X_{k-1}) is
     built block by block with rank truncation at 1e-10 of each block's norm
     (the paper's footnote leaves the replacement of X_{k-1} open); the
-    Rayleigh-Ritz matrix Q^T A Q is formed explicitly (the paper's LOBCG(+)).
+    Rayleigh-Ritz matrix Q^T A Q is formed explicitly (the paper's LOBCG(+));
+  * subspace tracking (the slowly varying operators of Sec. 1): each operator
+    of a sequence is solved from the previous one's final iterate, which the
+    solve orthonormalises again like any start block; the CG state (direction,
+    previous residual) starts afresh for every operator.
 """
 from __future__ import annotations
 
@@ -410,6 +414,21 @@ def solve(A, X0, opts: Options, record=False, callback=None):
         P, R_prev, rr_prev = D, R, rr
         k += 1
     return Result(X, Y, k, matvecs, converged, rel, restarts, history)
+
+
+def track(mats, X0, opts: Options, anorms=None):
+    """Subspace tracking over a sequence of operators A_0, A_1, ... (Sec. 1:
+    eigenspaces of slowly varying matrices, as in self-consistent-field
+    iterations): A_0 is solved from X0, every later A_k from the final
+    iterate X of A_{k-1}. Returns the list of Results."""
+    out = []
+    X = X0
+    for k, A in enumerate(mats):
+        o = opts if anorms is None else Options(**{**opts.__dict__, "anorm": float(anorms[k])})
+        r = solve(A, X, o)
+        out.append(r)
+        X = r.X
+    return out
 
 
 # ---------------------------------------------------------------------------

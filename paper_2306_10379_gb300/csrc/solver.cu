@@ -628,16 +628,9 @@ void fill_info(gsi_ctx* c, gsi_info* info) {
   info->trace = c->sign * tr;
 }
 
-// load X0 (float64, host or device), orthonormalise, Y = A X, clear the state
-gsi_status start(gsi_ctx* c, const double* X0, int on_device) {
-  const size_t blk = (size_t)blk_bytes(c);
-  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (c->emu) {
-    GSI_CUDA_TRY(cudaMemcpyAsync(c->W, X0, blk, kind, c->st));  // float64 staging in W
-    GSI_TRY(df_from_f64(c->n * c->p, (const double*)c->W, (float2*)c->X, c->st));
-  } else {
-    GSI_CUDA_TRY(cudaMemcpyAsync(c->X, X0, blk, kind, c->st));
-  }
+// the current X as a start block: orthonormalise it, Y = A X, clear the
+// iteration state and the counters
+gsi_status restart_state(gsi_ctx* c) {
   c->iters = c->matvecs = c->restarts = c->last_evals = 0;
   c->nd = c->mixed ? 3 : 7;
   c->y_fresh = true;
@@ -650,6 +643,130 @@ gsi_status start(gsi_ctx* c, const double* X0, int on_device) {
   GSI_TRY(op_matvec(c, c->X, c->Y));
   GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
   prof_harvest(c);
+  return GSI_OK;
+}
+
+// load X0 (float64, host or device), orthonormalise, Y = A X, clear the state
+gsi_status start(gsi_ctx* c, const double* X0, int on_device) {
+  const size_t blk = (size_t)blk_bytes(c);
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (c->emu) {
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->W, X0, blk, kind, c->st));  // float64 staging in W
+    GSI_TRY(df_from_f64(c->n * c->p, (const double*)c->W, (float2*)c->X, c->st));
+  } else {
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->X, X0, blk, kind, c->st));
+  }
+  return restart_state(c);
+}
+
+// (re)allocate a device buffer of the context: the old one (if any) is freed
+// and dropped from the context's list
+gsi_status realloc_dev(gsi_ctx* c, void** p, size_t bytes) {
+  if (*p) {
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), *p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  return dev_alloc(c, p, bytes);
+}
+
+// Copy the operator A into the context's device memory (sign applied for
+// which = -1), with its df64 copy and, for GSI_SELL, its SELL-C-sigma layout.
+// Buffers are (re)allocated when missing or when A's sizes differ from the
+// last operator's; c->n and c->fmt are already set.
+gsi_status upload_operator(gsi_ctx* c, const gsi_matrix* A) {
+  const int64_t n = c->n;
+  const int p = c->p;
+  cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (c->fmt == GSI_DENSE) {
+    const size_t nn = (size_t)n * n;
+    if (!c->Ad) GSI_TRY(dev_alloc(c, (void**)&c->Ad, nn * sizeof(double)));
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->Ad, A->val, nn * sizeof(double), kind, c->st));
+    if (c->sign < 0) {
+      scale_kernel<<<ceil_div((int64_t)nn, 256), 256, 0, c->st>>>((int64_t)nn, -1.0, c->Ad);
+      note_launch();
+      GSI_CUDA_TRY(cudaGetLastError());
+    }
+    if (c->emu) {
+      if (!c->Adf) GSI_TRY(dev_alloc(c, (void**)&c->Adf, nn * sizeof(float2)));
+      GSI_TRY(df_from_f64((int64_t)nn, c->Ad, c->Adf, c->st));
+      if (!c->dense_ws) GSI_TRY(dev_alloc(c, (void**)&c->dense_ws, oz_gram_scratch_bytes(n, (int)n, p, false)));
+    }
+    return GSI_OK;
+  }
+  const bool grow = !c->val || A->nnz != c->nnz;
+  c->nnz = A->nnz;
+  if (!c->rowptr) GSI_TRY(dev_alloc(c, (void**)&c->rowptr, (n + 1) * sizeof(int64_t)));
+  if (grow) {
+    GSI_TRY(realloc_dev(c, (void**)&c->colidx, c->nnz * sizeof(int32_t)));
+    GSI_TRY(realloc_dev(c, (void**)&c->val, c->nnz * sizeof(double)));
+    if (c->emu) GSI_TRY(realloc_dev(c, (void**)&c->vdf, c->nnz * sizeof(float2)));
+  }
+  GSI_CUDA_TRY(cudaMemcpyAsync(c->rowptr, A->rowptr, (n + 1) * sizeof(int64_t), kind, c->st));
+  GSI_CUDA_TRY(cudaMemcpyAsync(c->colidx, A->colidx, c->nnz * sizeof(int32_t), kind, c->st));
+  GSI_CUDA_TRY(cudaMemcpyAsync(c->val, A->val, c->nnz * sizeof(double), kind, c->st));
+  if (c->sign < 0 && c->nnz > 0) {
+    scale_kernel<<<ceil_div(c->nnz, 256), 256, 0, c->st>>>(c->nnz, -1.0, c->val);
+    note_launch();
+    GSI_CUDA_TRY(cudaGetLastError());
+  }
+  if (c->emu) GSI_TRY(df_from_f64(c->nnz, c->val, c->vdf, c->st));
+  if (c->fmt == GSI_SELL) {
+    c->C = A->sell_C > 0 ? A->sell_C : 32;
+    int sigma = A->sell_sigma > 0 ? A->sell_sigma : 32;
+    std::vector<int64_t> hrp(n + 1);
+    std::vector<int32_t> hci(c->nnz);
+    std::vector<double> hv(c->nnz);
+    GSI_CUDA_TRY(cudaMemcpyAsync(hrp.data(), c->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(hci.data(), c->colidx, c->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(hv.data(), c->val, c->nnz * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
+    int64_t nch = 0, total = 0;
+    GSI_TRY(gsi_sell_size(n, hrp.data(), c->C, sigma, &nch, &total));
+    std::vector<int64_t> perm(nch * c->C), cptr(nch + 1), clen(nch);
+    std::vector<int32_t> scol(total);
+    std::vector<double> sval(total);
+    GSI_TRY(gsi_csr_to_sell(n, hrp.data(), hci.data(), hv.data(), c->C, sigma, perm.data(), cptr.data(),
+                            clen.data(), scol.data(), sval.data()));
+    c->nchunks = nch;
+    GSI_TRY(realloc_dev(c, (void**)&c->perm, perm.size() * sizeof(int64_t)));
+    GSI_TRY(realloc_dev(c, (void**)&c->chunk_ptr, cptr.size() * sizeof(int64_t)));
+    GSI_TRY(realloc_dev(c, (void**)&c->chunk_len, clen.size() * sizeof(int64_t)));
+    GSI_TRY(realloc_dev(c, (void**)&c->scol, scol.size() * sizeof(int32_t)));
+    GSI_TRY(realloc_dev(c, (void**)&c->sval, sval.size() * sizeof(double)));
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->perm, perm.data(), perm.size() * 8, cudaMemcpyHostToDevice, c->st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->chunk_ptr, cptr.data(), cptr.size() * 8, cudaMemcpyHostToDevice, c->st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->chunk_len, clen.data(), clen.size() * 8, cudaMemcpyHostToDevice, c->st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->scol, scol.data(), scol.size() * 4, cudaMemcpyHostToDevice, c->st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->sval, sval.data(), sval.size() * 8, cudaMemcpyHostToDevice, c->st));
+    if (c->emu) {
+      GSI_TRY(realloc_dev(c, (void**)&c->sdf, sval.size() * sizeof(float2)));
+      GSI_TRY(df_from_f64((int64_t)sval.size(), c->sval, c->sdf, c->st));
+    }
+    GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  }
+  return GSI_OK;
+}
+
+// c->anorm: the given bound, else ||A||_inf of the context's operator
+gsi_status set_anorm(gsi_ctx* c, double anorm) {
+  if (anorm > 0) {
+    c->anorm = anorm;
+    return GSI_OK;
+  }
+  unsigned long long* d_mx = (unsigned long long*)c->dout;
+  GSI_CUDA_TRY(cudaMemsetAsync(d_mx, 0, 8, c->st));
+  if (c->fmt == GSI_DENSE) {
+    GSI_TRY(dense_absmax(c->n, c->Ad, d_mx, c->st));
+  } else {
+    csr_absmax_kernel<<<ceil_div(c->n, 256), 256, 0, c->st>>>(c->n, c->rowptr, c->val, d_mx);
+    note_launch();
+    GSI_CUDA_TRY(cudaGetLastError());
+  }
+  GSI_TRY(readback(c, c->dout, 1));
+  c->anorm = c->host[0];
+  if (!(c->anorm > 0)) c->anorm = 1.0;
   return GSI_OK;
 }
 
@@ -750,79 +867,7 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
     if (s != GSI_OK) goto fail; \
   } while (0)
   if (c->fmt == GSI_DENSE) c->nnz = 0;
-  {
-    cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (c->fmt == GSI_DENSE) {
-      const size_t nn = (size_t)n * n;
-      CK(dev_alloc(c, (void**)&c->Ad, nn * sizeof(double)));
-      CK(cuda_status_ok(cudaMemcpyAsync(c->Ad, A->val, nn * sizeof(double), kind, c->st)));
-      if (c->sign < 0) {
-        scale_kernel<<<ceil_div((int64_t)nn, 256), 256, 0, c->st>>>((int64_t)nn, -1.0, c->Ad);
-        note_launch();
-        CK(cuda_status_ok(cudaGetLastError()));
-      }
-      if (c->emu) {
-        CK(dev_alloc(c, (void**)&c->Adf, nn * sizeof(float2)));
-        CK(df_from_f64((int64_t)nn, c->Ad, c->Adf, c->st));
-        CK(dev_alloc(c, (void**)&c->dense_ws, oz_gram_scratch_bytes(n, (int)n, p, false)));
-      }
-    }
-  }
-  if (c->fmt != GSI_DENSE) {
-    cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(dev_alloc(c, (void**)&c->rowptr, (n + 1) * sizeof(int64_t)));
-    CK(dev_alloc(c, (void**)&c->colidx, c->nnz * sizeof(int32_t)));
-    CK(dev_alloc(c, (void**)&c->val, c->nnz * sizeof(double)));
-    CK(cuda_status_ok(cudaMemcpyAsync(c->rowptr, A->rowptr, (n + 1) * sizeof(int64_t), kind, c->st)));
-    CK(cuda_status_ok(cudaMemcpyAsync(c->colidx, A->colidx, c->nnz * sizeof(int32_t), kind, c->st)));
-    CK(cuda_status_ok(cudaMemcpyAsync(c->val, A->val, c->nnz * sizeof(double), kind, c->st)));
-    if (c->sign < 0 && c->nnz > 0) {
-      scale_kernel<<<ceil_div(c->nnz, 256), 256, 0, c->st>>>(c->nnz, -1.0, c->val);
-      note_launch();
-      CK(cuda_status_ok(cudaGetLastError()));
-    }
-    if (c->emu) {
-      CK(dev_alloc(c, (void**)&c->vdf, c->nnz * sizeof(float2)));
-      CK(df_from_f64(c->nnz, c->val, c->vdf, c->st));
-    }
-    if (c->fmt == GSI_SELL) {
-      c->C = A->sell_C > 0 ? A->sell_C : 32;
-      int sigma = A->sell_sigma > 0 ? A->sell_sigma : 32;
-      std::vector<int64_t> hrp(n + 1);
-      std::vector<int32_t> hci(c->nnz);
-      std::vector<double> hv(c->nnz);
-      CK(cuda_status_ok(cudaMemcpyAsync(hrp.data(), c->rowptr, (n + 1) * sizeof(int64_t),
-                                        cudaMemcpyDeviceToHost, c->st)));
-      CK(cuda_status_ok(cudaMemcpyAsync(hci.data(), c->colidx, c->nnz * sizeof(int32_t),
-                                        cudaMemcpyDeviceToHost, c->st)));
-      CK(cuda_status_ok(cudaMemcpyAsync(hv.data(), c->val, c->nnz * sizeof(double),
-                                        cudaMemcpyDeviceToHost, c->st)));
-      CK(cuda_status_ok(cudaStreamSynchronize(c->st)));
-      int64_t nch = 0, total = 0;
-      CK(gsi_sell_size(n, hrp.data(), c->C, sigma, &nch, &total));
-      std::vector<int64_t> perm(nch * c->C), cptr(nch + 1), clen(nch);
-      std::vector<int32_t> scol(total);
-      std::vector<double> sval(total);
-      CK(gsi_csr_to_sell(n, hrp.data(), hci.data(), hv.data(), c->C, sigma, perm.data(), cptr.data(),
-                         clen.data(), scol.data(), sval.data()));
-      c->nchunks = nch;
-      CK(dev_alloc(c, (void**)&c->perm, perm.size() * sizeof(int64_t)));
-      CK(dev_alloc(c, (void**)&c->chunk_ptr, cptr.size() * sizeof(int64_t)));
-      CK(dev_alloc(c, (void**)&c->chunk_len, clen.size() * sizeof(int64_t)));
-      CK(dev_alloc(c, (void**)&c->scol, scol.size() * sizeof(int32_t)));
-      CK(dev_alloc(c, (void**)&c->sval, sval.size() * sizeof(double)));
-      CK(cuda_status_ok(cudaMemcpyAsync(c->perm, perm.data(), perm.size() * 8, cudaMemcpyHostToDevice, c->st)));
-      CK(cuda_status_ok(cudaMemcpyAsync(c->chunk_ptr, cptr.data(), cptr.size() * 8, cudaMemcpyHostToDevice, c->st)));
-      CK(cuda_status_ok(cudaMemcpyAsync(c->chunk_len, clen.data(), clen.size() * 8, cudaMemcpyHostToDevice, c->st)));
-      CK(cuda_status_ok(cudaMemcpyAsync(c->scol, scol.data(), scol.size() * 4, cudaMemcpyHostToDevice, c->st)));
-      CK(cuda_status_ok(cudaMemcpyAsync(c->sval, sval.data(), sval.size() * 8, cudaMemcpyHostToDevice, c->st)));
-      if (c->emu) {
-        CK(dev_alloc(c, (void**)&c->sdf, sval.size() * sizeof(float2)));
-        CK(df_from_f64((int64_t)sval.size(), c->sval, c->sdf, c->st));
-      }
-      CK(cuda_status_ok(cudaStreamSynchronize(c->st)));
-    }
-  }
+  CK(upload_operator(c, A));
   {
     void* bufs[9];
     for (int i = 0; i < 9; ++i) CK(dev_alloc(c, &bufs[i], blk));
@@ -858,22 +903,7 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
     CK(oz_timeouts_async(c->tmo, c->st));
     CK(cuda_status_ok(cudaStreamSynchronize(c->st)));
     c->tmo_seen = *c->tmo;
-    if (opts.anorm > 0) {
-      c->anorm = opts.anorm;
-    } else {
-      unsigned long long* d_mx = (unsigned long long*)c->dout;
-      CK(cuda_status_ok(cudaMemsetAsync(d_mx, 0, 8, c->st)));
-      if (c->fmt == GSI_DENSE) {
-        CK(dense_absmax(n, c->Ad, d_mx, c->st));
-      } else {
-        csr_absmax_kernel<<<ceil_div(n, 256), 256, 0, c->st>>>(n, c->rowptr, c->val, d_mx);
-        note_launch();
-        CK(cuda_status_ok(cudaGetLastError()));
-      }
-      CK(readback(c, c->dout, 1));
-      c->anorm = c->host[0];
-      if (!(c->anorm > 0)) c->anorm = 1.0;
-    }
+    CK(set_anorm(c, opts.anorm));
     CK(timeout_check(c, start(c, X0, X0_on_device)));
   }
 #undef CK
@@ -887,6 +917,14 @@ fail:
 gsi_status gsi_reset(gsi_ctx* c, const double* X0, int32_t X0_on_device) {
   if (!c || !X0) return GSI_ERR_ARG;
   return timeout_check(c, start(c, X0, X0_on_device));
+}
+
+gsi_status gsi_set_operator(gsi_ctx* c, const gsi_matrix* A, double anorm) {
+  if (!c || !A || !A->val || A->fmt != c->fmt || A->n != c->n) return GSI_ERR_ARG;
+  if (A->fmt != GSI_DENSE && (!A->rowptr || !A->colidx || A->nnz < 0)) return GSI_ERR_ARG;
+  GSI_TRY(upload_operator(c, A));
+  GSI_TRY(set_anorm(c, anorm > 0 ? anorm : c->o.anorm));
+  return timeout_check(c, restart_state(c));
 }
 
 gsi_status gsi_step(gsi_ctx* c, int32_t nsteps, gsi_info* info) {

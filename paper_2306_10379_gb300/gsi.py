@@ -29,7 +29,8 @@ EXPORTED = [
     "gsi_csr_to_sell", "gsi_spmm_sell", "gsi_gram", "gsi_residual", "gsi_linesearch",
     "gsi_retract", "gsi_df_spmm_csr", "gsi_oz_gemm", "gsi_oz_gram", "gsi_reset",
     "gsi_profile_enable", "gsi_profile_read", "gsi_launch_count", "gsi_oz_dense_apply",
-    "gsi_oz_gram_noalloc", "gsi_measure_fma_peaks",
+    "gsi_oz_gram_noalloc", "gsi_measure_fma_peaks", "gsi_set_operator", "gsi_set_wait_limit",
+    "gsi_device_timeouts",
 ]
 
 
@@ -130,6 +131,7 @@ def _lib():
             "gsi_gemm_bf16": [i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, ctypes.c_float,
                               ctypes.c_float, vp, vp, i32, vp],
             "gsi_set_wait_limit": [i32],
+            "gsi_set_operator": [vp, ctypes.POINTER(Matrix), dbl],
             "gsi_device_timeouts": [ctypes.POINTER(i64)],
             "gsi_profile_enable": [vp, i32],
             "gsi_profile_read": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
@@ -381,6 +383,34 @@ class Dense:
         self.n = int(val.shape[0])
 
 
+def _matrix(A, fmt, keep):
+    """gsi_matrix for A (object with n, rowptr, colidx, val as numpy host arrays
+    or torch CUDA tensors; or gsi.Dense); host arrays are kept alive in keep."""
+    import torch
+    dense = getattr(A, "dense", False)
+    on_dev = isinstance(A.val, torch.Tensor)
+    if dense:
+        if on_dev:
+            va = _dptr(A.val, torch.float64, (A.n, A.n))
+        else:
+            arr = np.ascontiguousarray(A.val, np.float64)
+            keep.append(arr)
+            va = ctypes.c_void_p(arr.ctypes.data)
+        rp = ci = None
+        nnz = 0
+    elif on_dev:
+        rp, ci, va = _dptr(A.rowptr, torch.int64), _dptr(A.colidx, torch.int32), _dptr(A.val, torch.float64)
+        nnz = int(A.colidx.numel())
+    else:
+        arrs = [np.ascontiguousarray(A.rowptr, np.int64), np.ascontiguousarray(A.colidx, np.int32),
+                np.ascontiguousarray(A.val, np.float64)]
+        keep += arrs
+        rp, ci, va = (ctypes.c_void_p(a.ctypes.data) for a in arrs)
+        nnz = int(arrs[1].size)
+    fm = GSI_DENSE if dense else (GSI_SELL if fmt == "sell" else GSI_CSR)
+    return Matrix(fm, int(A.n), nnz, rp, ci, va, 32, 32, 1 if on_dev else 0)
+
+
 class Solver:
     """gsi_create / gsi_step / gsi_solve / gsi_get_basis / gsi_destroy.
 
@@ -394,28 +424,8 @@ class Solver:
         import torch
         L = lib()
         self._keep = []
-        dense = getattr(A, "dense", False)
-        on_dev = isinstance(A.val, torch.Tensor)
-        if dense:
-            if on_dev:
-                va = _dptr(A.val, torch.float64, (A.n, A.n))
-            else:
-                arr = np.ascontiguousarray(A.val, np.float64)
-                self._keep.append(arr)
-                va = ctypes.c_void_p(arr.ctypes.data)
-            rp = ci = None
-            nnz = 0
-        elif on_dev:
-            rp, ci, va = _dptr(A.rowptr, torch.int64), _dptr(A.colidx, torch.int32), _dptr(A.val, torch.float64)
-            nnz = int(A.colidx.numel())
-        else:
-            arrs = [np.ascontiguousarray(A.rowptr, np.int64), np.ascontiguousarray(A.colidx, np.int32),
-                    np.ascontiguousarray(A.val, np.float64)]
-            self._keep += arrs
-            rp, ci, va = (ctypes.c_void_p(a.ctypes.data) for a in arrs)
-            nnz = int(arrs[1].size)
-        fm = GSI_DENSE if dense else (GSI_SELL if fmt == "sell" else GSI_CSR)
-        m = Matrix(fm, int(A.n), nnz, rp, ci, va, 32, 32, 1 if on_dev else 0)
+        self._fmt = fmt
+        m = _matrix(A, fmt, self._keep)
         o = Opts()
         L.gsi_default_opts(ctypes.byref(o))
         o.method = {"sd": GSI_SD, "cg": GSI_CG, "cheb": GSI_CHEB}[method]
@@ -452,6 +462,13 @@ class Solver:
         info = Info()
         _check(lib().gsi_step(self._ctx, int(nsteps), ctypes.byref(info)), "gsi_step")
         return info.as_dict()
+
+    def set_operator(self, A, anorm=0.0):
+        """gsi_set_operator: the next problem of a sequence (same n and format),
+        started from the current iterate."""
+        keep = []
+        m = _matrix(A, self._fmt, keep)
+        _check(lib().gsi_set_operator(self._ctx, ctypes.byref(m), float(anorm)), "gsi_set_operator")
 
     def solve(self, raise_on_noconv=False):
         info = Info()

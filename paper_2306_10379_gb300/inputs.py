@@ -153,6 +153,27 @@ def fd_laplacian(dims) -> CSR:
     return CSR(n, rowptr, cols[valid].astype(np.int32), vals[valid])
 
 
+def drifting_laplacians(dims, count: int, eps: float) -> list:
+    """A slowly varying sequence for subspace tracking: A_k = L + eps k diag(v),
+    k = 0..count-1, L = fd_laplacian(dims) and v the smooth potential
+    v(x) = prod over axes of sin(pi x_a) cos(pi x_a) at the nodes
+    x_a = (i_a + 1)/(d_a + 1). Same sparsity for every k (L's diagonal)."""
+    L = fd_laplacian(dims)
+    # node index i0 + d0 i1 (+ d0 d1 i2): the first axis varies fastest
+    v = np.ones(1)
+    for d in dims:
+        x = (np.arange(d) + 1.0) / (d + 1.0)
+        v = np.kron(np.sin(np.pi * x) * np.cos(np.pi * x), v)
+    rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
+    diag = np.flatnonzero(L.colidx == rows)
+    out = []
+    for k in range(count):
+        val = L.val.copy()
+        val[diag] += eps * k * v[rows[diag]]
+        out.append(CSR(L.n, L.rowptr.copy(), L.colidx.copy(), val))
+    return out
+
+
 def er_laplacian(n: int, seed: int, mean_degree: int = 8) -> CSR:
     """Graph Laplacian D - W of an Erdos-Renyi G(n, M) graph, M = n*mean_degree/2
     distinct undirected unit-weight edges drawn in Philox order (self-loops and

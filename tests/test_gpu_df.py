@@ -30,7 +30,7 @@ def _exact(gsi, x):
     return gsi.from_df(gsi.to_df(x))
 
 
-@pytest.mark.parametrize("p", [1, 7, 64])
+@pytest.mark.parametrize("p", [1, 2, 7, 8, 16, 32, 64, 100, 128])
 def test_df_spmm(G, p):
     torch, gsi = G
     A = I.er_laplacian(20011, 3)
@@ -43,6 +43,39 @@ def test_df_spmm(G, p):
     got = gsi.from_df(W.cpu().numpy())
     ref = O.spmm(S, X)
     assert np.all(np.abs(got - ref) <= 1e-13 * O.spmm(abs(S), np.abs(X)))
+
+
+def test_df_spmm_empty_rows_and_unaligned_blocks(G):
+    """Rows without nonzeros give zero rows; blocks that are not 16-byte
+    aligned take the per-column-pair kernel, which sums in the same order as
+    the row-group kernel: bit-identical results."""
+    torch, gsi = G
+    p = 64
+    A = I.er_laplacian(5003, 11)
+    rp = A.rowptr.copy()
+    keep = np.ones(A.nnz, bool)
+    empty = np.arange(0, A.n, 97)
+    for r in empty:  # drop every nonzero of these rows
+        keep[rp[r]:rp[r + 1]] = False
+    cnt = np.diff(rp).copy()
+    cnt[empty] = 0
+    rowptr = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    colidx, val = A.colidx[keep], A.val[keep]
+    X = _exact(gsi, I.start_block(A.n, p, 2))
+    S = O.csr_operator(A.n, rowptr, colidx, val)
+    args = (torch.from_numpy(rowptr).cuda(), torch.from_numpy(colidx).cuda(), _df_dev(torch, gsi, val))
+    W = torch.empty((A.n, p, 2), dtype=torch.float32, device="cuda")
+    gsi.df_spmm_csr(*args, _df_dev(torch, gsi, X), W)
+    got = gsi.from_df(W.cpu().numpy())
+    assert np.all(got[empty] == 0.0)
+    assert np.all(np.abs(got - O.spmm(S, X)) <= 1e-13 * O.spmm(abs(S), np.abs(X)))
+    # the same product from blocks 8 bytes off a 16-byte boundary
+    xb = torch.empty((A.n * p + 1, 2), dtype=torch.float32, device="cuda")
+    wb = torch.empty((A.n * p + 1, 2), dtype=torch.float32, device="cuda")
+    Xu, Wu = xb[1:].view(A.n, p, 2), wb[1:].view(A.n, p, 2)
+    Xu.copy_(_df_dev(torch, gsi, X))
+    gsi.df_spmm_csr(*args, Xu, Wu)
+    assert torch.equal(Wu, W)
 
 
 @pytest.mark.parametrize("n,p,nk,ne", [(1, 1, 1, 0), (33, 8, 1, 1), (1000, 17, 2, 2), (100003, 64, 1, 1),

@@ -388,3 +388,25 @@ def test_residual_inf_matches_oracle(torch_cuda, dims, p, precision):
             assert abs(got - want) <= rel * want + 1e-9, (k, got, want)
             worst = max(worst, abs(got - want) / want)
     assert hist[-1].res_inf < hist[0].res_inf  # the criterion moved over the 10 steps
+
+
+@pytest.mark.parametrize("precision", ["df64", "f64"])
+def test_iteration_count_3d_matches_oracle(torch_cuda, precision):
+    """The bench's form (3D 7-point Laplacian, p = 64, CG, CSR) at a size the
+    oracle solves in seconds: 18 x 20 x 22 (n = 7920, gap lambda_64 -
+    lambda_65 = 1.0e-2). Whole-solve iteration counts within 2% of the
+    oracle's from the same start block, Ritz values within 1e-10 of the
+    closed form."""
+    from paper_2306_10379_gb300 import gsi
+    dims, p = (18, 20, 22), 64
+    A = I.fd_laplacian(dims)
+    lam = I.laplacian_eigenvalues(dims)
+    X0 = I.start_block(A.n, p, I.SEED_BASE + 1)
+    with gsi.Solver(A, p, X0, method="cg", tol=1e-8, anorm=lam[0], precision=precision) as s:
+        info = s.solve()
+        _, ev = s.basis()
+    ores = O.solve(O.csr_operator(A.n, A.rowptr, A.colidx, A.val), X0,
+                   O.Options(method="cg", tol=1e-8, anorm=lam[0]))
+    assert info["converged"] == 1 and ores.converged
+    assert abs(info["iters"] - ores.iters) <= max(2, 0.02 * ores.iters), (info["iters"], ores.iters)
+    assert np.max(np.abs(ev - lam[:p]) / lam[:p]) < 1e-10
