@@ -46,8 +46,16 @@ typedef enum {
 
 typedef enum { GSI_CSR = 0, GSI_SELL = 1, GSI_DENSE = 2 } gsi_format;
 /* GSI_CHEB: the Chebyshev-filtered subspace iteration the paper compares
- * against (Alg. 1 with the filter of Eq. (optimal_poly)). */
-typedef enum { GSI_SD = 0, GSI_CG = 1, GSI_CHEB = 2 } gsi_method;
+ * against (Alg. 1 with the filter of Eq. (optimal_poly)).
+ * GSI_LOBCG: the locally optimal block CG method the paper compares against
+ * (Sec. 6.4, Eq. (def_Vk_LOBPCG)) in its LOBCG(+) form: every iteration the
+ * Rayleigh-Ritz procedure on span(X_k, G_k, P_k), P_k the part of X_k outside
+ * span(X_{k-1}) (the better-conditioned block that replaces X_{k-1}), with
+ * each block orthonormalised from its Gram matrix (singular values below
+ * 1e-7 of the block's largest dropped) and Q^T A Q formed from explicit
+ * products with A Q: three block matvecs per iteration. p <= 64 (the
+ * 3p x 3p eigenproblem runs in one thread block in float64). */
+typedef enum { GSI_SD = 0, GSI_CG = 1, GSI_CHEB = 2, GSI_LOBCG = 3 } gsi_method;
 /* Arithmetic of the n x p block work. GSI_PREC_DF64: blocks stored as
  * float32 pairs (48-bit significand), products on the BF16 tensor cores with
  * error-free digit splitting into 7 digits (float64-class results);
@@ -83,7 +91,7 @@ typedef struct {
 } gsi_matrix;
 
 typedef struct {
-  int32_t method;          /* GSI_SD (Alg. 2) or GSI_CG (Alg. 4) */
+  int32_t method;          /* GSI_SD (Alg. 2), GSI_CG (Alg. 4), GSI_CHEB or GSI_LOBCG */
   int32_t which;           /* +1: largest p eigenvalues; -1: smallest (runs on -A) */
   double tol;              /* stop when ||R||_F / anorm <= tol (default 1e-8) */
   double anorm;            /* ||A||_2 or an upper bound; <= 0: ||A||_inf is used */

@@ -33,10 +33,14 @@ Readings of points the paper leaves open:
     X + tD (both equal the paper's expressions in exact arithmetic);
   * AX is recomputed explicitly when t*sqrt(beta_max) < 1e3*eps, every
     `recompute_every` iterations, and before the final residual;
-  * LOBCG (the comparator of Sec. 6.4): the basis of span(X_k, G_k, X_{k-1}) is
-    built block by block with rank truncation at 1e-10 of each block's norm
-    (the paper's footnote leaves the replacement of X_{k-1} open); the
-    Rayleigh-Ritz matrix Q^T A Q is formed explicitly (the paper's LOBCG(+));
+  * LOBCG (the comparator of Sec. 6.4): X_{k-1} is replaced by the momentum
+    block P_k of Knyazev's method (the part of X_k outside span(X_{k-1}); the
+    paper's footnote says a better-conditioned block replaces X_{k-1} without
+    naming it), which spans the same V_k; the basis of span(X_k, G_k, P_k) is
+    built block by block from Gram matrices (the paper's implementation
+    orthonormalises by Cholesky) with rank truncation at 1e-7 of each block's
+    largest singular value; the Rayleigh-Ritz matrix Q^T A Q is formed
+    explicitly (the paper's LOBCG(+));
   * subspace tracking (the slowly varying operators of Sec. 1): each operator
     of a sequence is solved from the previous one's final iterate, which the
     solve orthonormalises again like any start block; the CG state (direction,
@@ -435,48 +439,67 @@ def track(mats, X0, opts: Options, anorms=None):
 # LOBCG comparator (Sec. 6.4, "Comparison to LOBCG"; Knyazev 2001)
 # ---------------------------------------------------------------------------
 
-def block_basis(blocks, rank_tol=1e-10):
+LOBCG_RANK_TOL = 1e-7
+
+
+def block_basis(blocks, rank_tol=LOBCG_RANK_TOL):
     """Orthonormal basis of the column span of the blocks, built block by
-    block: each block is projected off the basis so far (twice), and its left
-    singular vectors with singular values above rank_tol times the block's
-    own norm are appended. Near convergence X_{k-1} lies almost in span(X_k),
-    the cancellation of the paper's footnote to Eq. (def_Vk_LOBPCG); the
-    truncation drops what is left of it at rounding level."""
+    block as the paper's implementation does it, by orthonormalisations of
+    Gram matrices (Sec. 6.4: three per iteration, by Cholesky): each block B
+    is projected off the basis so far (twice); with its Gram
+    S = B^T B = U diag(s) U^T (eigenvalues descending), B U_r diag(s_r)^(-1/2)
+    over the eigenvalues s_i > rank_tol^2 s_1 spans what is left of B (its
+    singular values above rank_tol times the largest), and a second pass
+    Q <- Q (Q^T Q)^(-1/2) restores orthonormality to rounding level. A Gram
+    resolves singular values down to about sqrt(eps) of the largest, hence
+    rank_tol = 1e-7. Returns (Q, widths)."""
     Q = np.zeros((blocks[0].shape[0], 0))
+    widths = []
     for B in blocks:
-        bn = np.linalg.norm(B, 2)
-        if bn == 0.0:
-            continue
         for _ in range(2):
             B = B - Q @ (Q.T @ B)
-        U, s, _ = np.linalg.svd(B, full_matrices=False)
-        Q = np.hstack([Q, U[:, s > rank_tol * bn]])
-    return Q
+        s, U = np.linalg.eigh(B.T @ B)
+        s, U = s[::-1], U[:, ::-1]
+        keep = s > rank_tol ** 2 * s[0] if s[0] > 0.0 else np.zeros(s.size, bool)
+        Qb = B @ (U[:, keep] / np.sqrt(s[keep]))
+        if Qb.shape[1]:
+            Qb = Qb @ inverse_sqrt(Qb.T @ Qb)
+        Q = np.hstack([Q, Qb])
+        widths.append(Qb.shape[1])
+    return Q, widths
 
 
-def lobcg_step(A, X, X_prev=None):
+def lobcg_step(A, X, W=None):
     """One LOBCG step: the Rayleigh-Ritz procedure for A on
-    V_k = span(X_k, G_k, X_{k-1}) (Eq. (def_Vk_LOBPCG)), G_k = A X_k - X_k C_k
-    the gradient direction; the next iterate is the Ritz vectors of the p
-    largest Ritz values (the maximisation of the partial trace; the minimum
-    problem runs on -A as in Sec. 2.1)."""
+    V_k = span(X_k, G_k, W) (Eq. (def_Vk_LOBPCG)), G_k = A X_k - X_k C_k the
+    gradient direction and W the momentum block: X_{k-1} itself, or -- the
+    better-conditioned block the paper's footnote to that equation refers to
+    (Knyazev 2001) -- P_k, the part of X_k outside span(X_{k-1}) from the
+    previous step; both give the same V_k. The next iterate is the Ritz
+    vectors of the p largest Ritz values (the maximisation of the partial
+    trace; the minimum problem runs on -A as in Sec. 2.1). Returns
+    (X_{k+1}, P_{k+1}), P_{k+1} = X_{k+1} minus its component in span(X_k)."""
     Y = spmm(A, X)
     C = gram(X, Y)
     G = Y - X @ (0.5 * (C + C.T))
-    Q = block_basis([X, G] + ([X_prev] if X_prev is not None else []))
+    Q, widths = block_basis([X, G] + ([W] if W is not None else []))
     H = gram(Q, spmm(A, Q))
     w, V = np.linalg.eigh(0.5 * (H + H.T))
-    return Q @ V[:, np.argsort(w)[::-1][:X.shape[1]]]
+    V = V[:, np.argsort(w)[::-1][:X.shape[1]]]
+    w1 = widths[0]
+    return Q @ V, Q[:, w1:] @ V[w1:, :]
 
 
-def lobcg_solve(A, X0, tol=1e-8, anorm=0.0, max_iters=10000):
-    """LOBCG from the orthonormalised X0: X_{k+1} = lobcg_step(A, X_k, X_{k-1})
-    (no X_{-1} in the first step), with the stopping test of solve():
-    ||A X_k - X_k C_k||_F <= tol * anorm."""
+def lobcg_solve(A, X0, tol=1e-8, anorm=0.0, max_iters=10000, record=False):
+    """LOBCG from the orthonormalised X0: (X_{k+1}, P_{k+1}) =
+    lobcg_step(A, X_k, P_k) (no momentum block in the first step), with the
+    stopping test of solve(): ||A X_k - X_k C_k||_F <= tol * anorm. record:
+    the Result's history holds each iterate X_k (k >= 1)."""
     anorm = anorm if anorm > 0 else anorm_inf(A)
     X = orthonormalize(X0)
-    X_prev = None
+    P = None
     k = 0
+    hist = []
     while True:
         Y = spmm(A, X)
         C = gram(X, Y)
@@ -484,9 +507,11 @@ def lobcg_solve(A, X0, tol=1e-8, anorm=0.0, max_iters=10000):
         rel = math.sqrt(float(np.sum(R * R))) / anorm
         if rel <= tol or k >= max_iters:
             break
-        X, X_prev = lobcg_step(A, X, X_prev), X
+        X, P = lobcg_step(A, X, P)
+        if record:
+            hist.append(X.copy())
         k += 1
-    return Result(X, Y, k, k + 1, rel <= tol, rel, 0)
+    return Result(X, Y, k, k + 1, rel <= tol, rel, 0, hist)
 
 
 # ---------------------------------------------------------------------------

@@ -58,4 +58,13 @@ gsi_status small_step_df(int mode, int p, const double* C, const double* B, cons
 gsi_status small_eig(int p, const double* C, double* theta, double* U, double* scratch,
                      cudaStream_t st);
 
+// LOBCG comparator helpers (lobcg.cu)
+gsi_status lobcg_coef(int p, const double* theta, const double* U, double tol2, double* M, int* mask,
+                      cudaStream_t st);
+gsi_status lobcg_mask_gram(int p, double* S, const int* mask, cudaStream_t st);
+gsi_status lobcg_assemble(int p, int nb, const double* H11, const double* H12, const double* H13,
+                          const double* H22, const double* H23, const double* H33, const int* mask2,
+                          const int* mask3, double sentinel, double* H, cudaStream_t st);
+gsi_status lobcg_split(int p, int nb, const double* U, double* V1, double* V2, double* V3, cudaStream_t st);
+
 }  // namespace gsi

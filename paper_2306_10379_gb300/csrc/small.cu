@@ -15,6 +15,7 @@
 namespace gsi {
 
 constexpr int SMALL_THREADS = 512;
+constexpr int SMALL_EIG_MAX = 192;
 
 size_t small_scratch_doubles(int p) { return (size_t)5 * p * p + 5 * (size_t)p + 64; }
 
@@ -98,13 +99,14 @@ gsi_status small_step(int mode, int p, const double* C, const double* B, const d
 }
 
 // Rayleigh-Ritz (Eq. (rr1)): theta descending and U (columns) with
-// (C + C^T)/2 = U diag(theta) U^T.
+// (C + C^T)/2 = U diag(theta) U^T; p <= SMALL_EIG_MAX (the 3p x 3p
+// Rayleigh-Ritz matrix of LOBCG at p <= 64).
 __global__ void __launch_bounds__(SMALL_THREADS)
 small_eig_kernel(int p, const double* C, double* theta, double* Uout, double* ws) {
-  __shared__ double rc[64], rs[64];
-  __shared__ int ri[64], rj[64];
+  __shared__ double rc[SMALL_EIG_MAX / 2], rs[SMALL_EIG_MAX / 2];
+  __shared__ int ri[SMALL_EIG_MAX / 2], rj[SMALL_EIG_MAX / 2];
   __shared__ double red[64];
-  __shared__ int order[128];
+  __shared__ int order[SMALL_EIG_MAX];
   SmallWs w = carve(ws, p);
   const int q = p * p;
   for (int e = threadIdx.x; e < q; e += blockDim.x) {
@@ -135,7 +137,7 @@ small_eig_kernel(int p, const double* C, double* theta, double* Uout, double* ws
 
 gsi_status small_eig(int p, const double* C, double* theta, double* U, double* scratch,
                      cudaStream_t st) {
-  if (p < 1 || p > 128) return GSI_ERR_ARG;
+  if (p < 1 || p > SMALL_EIG_MAX) return GSI_ERR_ARG;
   small_eig_kernel<<<1, SMALL_THREADS, 0, st>>>(p, C, theta, U, scratch);
   GSI_LAUNCH_CHECK();
   return GSI_OK;

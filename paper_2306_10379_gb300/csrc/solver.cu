@@ -137,6 +137,11 @@ struct gsi_ctx {
   void* eig_ws = nullptr;
   int gram_reserve = 0;  // SMs the next Grams leave free
   double* host = nullptr;  // pinned readback buffer
+  // LOBCG comparator: p x p workspace, masks of the kept columns of the
+  // second and third basis blocks, and the eigensolver's scratch for 3p x 3p
+  double* lob = nullptr;
+  int* lob_mask = nullptr;
+  double* lob_ws = nullptr;
   int* tmo = nullptr;      // pinned copy of the tensor-core kernels' timeout count
   int tmo_seen = 0;        // that count when this context last looked
   std::vector<void*> allocs;
@@ -609,6 +614,131 @@ gsi_status iterate_cheb(gsi_ctx* c, bool* stop) {
   return GSI_OK;
 }
 
+// ---- LOBCG comparator (Sec. 6.4, "Comparison to LOBCG") ------------------
+
+constexpr double LOBCG_RANK_TOL = 1e-7;  // kept singular values, relative to a block's largest
+
+// p x p slots of the LOBCG workspace
+struct LobWs {
+  double *K1, *K2, *S, *U, *M2, *M3, *H12, *H13, *H22, *H23, *H33, *V1, *V2, *V3, *H, *th;
+};
+LobWs lob_ws(gsi_ctx* c) {
+  const size_t q = (size_t)c->p * c->p;
+  double* L = c->lob;
+  return {L, L + q, L + 2 * q, L + 3 * q, L + 12 * q, L + 13 * q, L + 14 * q, L + 15 * q, L + 16 * q,
+          L + 17 * q, L + 18 * q, L + 19 * q, L + 20 * q, L + 21 * q, L + 22 * q, L + 31 * q};
+}
+size_t lob_doubles(int p) { return (size_t)31 * p * p + 3 * (size_t)p + 64; }
+
+// One basis block of V_k in place of *B: projected off Q1 (and Q2) twice;
+// from the eigendecomposition of its Gram B^T B = U diag(th) U^T,
+// B U_r diag(th_r)^(-1/2) over th_i > tol^2 th_0 (dropped columns zero,
+// mask 0); then Q <- Q (Q^T Q)^(-1/2) on the kept columns.
+gsi_status lob_block(gsi_ctx* c, void** B, const void* Q1, const void* Q2, double* M, int* mask) {
+  const int p = c->p;
+  LobWs w = lob_ws(c);
+  for (int pass = 0; pass < 2; ++pass) {
+    GSI_TRY(op_gram(c, Q1, *B, false, w.K1));
+    if (Q2) GSI_TRY(op_gram(c, Q2, *B, false, w.K2));
+    GSI_TRY(op_blockmul(c, Q2 ? 2 : 1, Q1, w.K1, -1.0, Q2, Q2 ? w.K2 : nullptr, -1.0, 1, *B, 1.0, nullptr, 0.0,
+                        *B, false, nullptr));
+  }
+  GSI_TRY(op_gram(c, *B, *B, true, w.S));
+  prof_begin(c);
+  GSI_TRY(small_eig(p, w.S, w.th, w.U, c->lob_ws, c->st));
+  GSI_TRY(lobcg_coef(p, w.th, w.U, LOBCG_RANK_TOL * LOBCG_RANK_TOL, M, mask, c->st));
+  prof_end(c, GSI_K_SMALL, 0.0, 0.0);
+  GSI_TRY(op_blockmul(c, 1, *B, M, 1.0, nullptr, nullptr, 0.0, 0, nullptr, 0.0, nullptr, 0.0, c->Yn, false,
+                      nullptr));
+  std::swap(*B, c->Yn);
+  GSI_TRY(op_gram(c, *B, *B, true, w.S));
+  prof_begin(c);
+  GSI_TRY(lobcg_mask_gram(p, w.S, mask, c->st));
+  prof_end(c, GSI_K_SMALL, 0.0, 0.0);
+  GSI_TRY(op_small(c, 1, w.S, w.S));  // Mm = S^(-1/2)
+  GSI_TRY(readback(c, c->out, 5));
+  if (c->host[3] != 0.0) return GSI_ERR_BREAKDOWN;
+  GSI_TRY(op_blockmul(c, 1, *B, c->Mm, 1.0, nullptr, nullptr, 0.0, 0, nullptr, 0.0, nullptr, 0.0, c->Yn, false,
+                      nullptr));
+  std::swap(*B, c->Yn);
+  return GSI_OK;
+}
+
+// One LOBCG iteration (the comparator of Sec. 6.4, in its LOBCG(+) form):
+// the Rayleigh-Ritz procedure on V_k = span(X_k, G_k, P_k) (Eq.
+// (def_Vk_LOBPCG)), G_k = A X_k - X_k C_k and P_k the part of X_k outside
+// span(X_{k-1}) (Knyazev's block, which the paper's footnote puts in place of
+// X_{k-1}; same V_k). Buffers: Q1 = X (AQ1 = Y, explicit every iteration),
+// Q2 in R (AQ2 in W), Q3 in D (AQ3 in Rp), P in P. Q^T A Q is formed from
+// its six p x p blocks (explicit products with A Q, the paper's LOBCG(+));
+// its top p eigenvectors give X_{k+1} = Q1 V1 + Q2 V2 + Q3 V3 and
+// P_{k+1} = Q2 V2 + Q3 V3.
+gsi_status iterate_lobcg(gsi_ctx* c, bool* stop) {
+  const int p = c->p;
+  *stop = false;
+  LobWs w = lob_ws(c);
+  GSI_TRY(op_gram(c, c->X, c->Y, true, c->Cm));
+  GSI_TRY(op_blockmul(c, 1, c->X, c->Cm, -1.0, nullptr, nullptr, 0.0, 1, c->Y, 1.0, nullptr, 0.0, c->R, true,
+                      nullptr, true));
+  const bool rinf_fused = c->rinf_fused;
+  GSI_TRY(readback(c, c->dout, rinf_fused ? 3 : 2));
+  const double rr = c->host[0];
+  double rinf = rinf_fused ? c->host[2] : 0.0;
+  if (!rinf_fused) {
+    GSI_TRY(op_rowinf(c, c->R));
+    GSI_TRY(readback(c, c->dout + 2, 1));
+    rinf = c->host[0];
+  }
+  if (!isfinite(rr)) return GSI_ERR_NONFINITE;
+  if (c->res0_inf < 0.0) c->res0_inf = rinf;
+  c->rel = sqrt(rr) / c->anorm;
+  c->rel_inf = c->res0_inf > 0.0 ? rinf / c->res0_inf : 0.0;
+  if (c->rel <= c->o.tol || c->iters >= c->o.max_iters) {
+    c->converged = c->rel <= c->o.tol;
+    *stop = true;
+    return GSI_OK;
+  }
+  const bool prev = c->have_prev;
+  GSI_TRY(lob_block(c, &c->R, c->X, nullptr, w.M2, c->lob_mask));
+  GSI_TRY(op_matvec(c, c->R, c->W));
+  if (prev) {
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->D, c->P, (size_t)blk_bytes(c), cudaMemcpyDeviceToDevice, c->st));
+    GSI_TRY(lob_block(c, &c->D, c->X, c->R, w.M3, c->lob_mask + p));
+    GSI_TRY(op_matvec(c, c->D, c->Rp));
+  }
+  GSI_TRY(op_gram(c, c->X, c->W, false, w.H12));
+  GSI_TRY(op_gram(c, c->R, c->W, true, w.H22));
+  if (prev) {
+    GSI_TRY(op_gram(c, c->X, c->Rp, false, w.H13));
+    GSI_TRY(op_gram(c, c->R, c->Rp, false, w.H23));
+    GSI_TRY(op_gram(c, c->D, c->Rp, true, w.H33));
+  }
+  const int nb = prev ? 3 : 2;
+  prof_begin(c);
+  GSI_TRY(lobcg_assemble(p, nb, c->Cm, w.H12, w.H13, w.H22, w.H23, w.H33, c->lob_mask, c->lob_mask + p,
+                         -(10.0 * c->anorm + 1.0), w.H, c->st));
+  GSI_TRY(small_eig(nb * p, w.H, w.th, w.U, c->lob_ws, c->st));
+  GSI_TRY(lobcg_split(p, nb, w.U, w.V1, w.V2, w.V3, c->st));
+  prof_end(c, GSI_K_SMALL, 0.0, 0.0);
+  GSI_TRY(op_blockmul(c, prev ? 2 : 1, c->R, w.V2, 1.0, prev ? c->D : nullptr, prev ? w.V3 : nullptr, 1.0, 0,
+                      nullptr, 0.0, nullptr, 0.0, c->Yn, false, nullptr));
+  GSI_TRY(op_blockmul(c, 1, c->X, w.V1, 1.0, nullptr, nullptr, 0.0, 1, c->Yn, 1.0, nullptr, 0.0, c->Xn, false,
+                      nullptr));
+  std::swap(c->X, c->Xn);
+  std::swap(c->P, c->Yn);
+  GSI_TRY(op_matvec(c, c->X, c->Y));
+  c->y_fresh = true;
+  c->have_prev = true;
+  c->iters++;
+  return GSI_OK;
+}
+
+gsi_status iterate_any(gsi_ctx* c, bool* stop) {
+  if (c->o.method == GSI_CHEB) return iterate_cheb(c, stop);
+  if (c->o.method == GSI_LOBCG) return iterate_lobcg(c, stop);
+  return iterate(c, stop);
+}
+
 void fill_info(gsi_ctx* c, gsi_info* info) {
   if (!info) return;
   info->iters = c->iters;
@@ -840,7 +970,8 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
   if (opts.method == GSI_CHEB &&
       (opts.cheb_degree < 1 || !(opts.cheb_hi > opts.cheb_lo) || !(opts.cheb_scale > opts.cheb_hi)))
     return GSI_ERR_ARG;
-  if ((opts.method != GSI_SD && opts.method != GSI_CG && opts.method != GSI_CHEB) ||
+  if (opts.method == GSI_LOBCG && p > 64) return GSI_ERR_ARG;
+  if ((opts.method != GSI_SD && opts.method != GSI_CG && opts.method != GSI_CHEB && opts.method != GSI_LOBCG) ||
       (opts.which != 1 && opts.which != -1) ||
       opts.max_iters < 0 || !(opts.tol >= 0.0) ||
       (opts.precision != GSI_PREC_DF64 && opts.precision != GSI_PREC_F64 &&
@@ -898,6 +1029,11 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
       CK(cuda_status_ok(cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming)));
       CK(cuda_status_ok(cudaEventCreateWithFlags(&c->ev_e, cudaEventDisableTiming)));
     }
+    if (opts.method == GSI_LOBCG) {
+      CK(dev_alloc(c, (void**)&c->lob, lob_doubles(p) * sizeof(double)));
+      CK(dev_alloc(c, (void**)&c->lob_mask, 2 * (size_t)p * sizeof(int)));
+      CK(dev_alloc(c, (void**)&c->lob_ws, small_scratch_doubles(3 * p) * sizeof(double)));
+    }
     CK(cuda_status_ok(cudaMallocHost((void**)&c->host, std::max<size_t>(q, 64) * sizeof(double))));
     CK(cuda_status_ok(cudaMallocHost((void**)&c->tmo, 64)));
     CK(oz_timeouts_async(c->tmo, c->st));
@@ -931,7 +1067,7 @@ gsi_status gsi_step(gsi_ctx* c, int32_t nsteps, gsi_info* info) {
   if (!c || nsteps < 0) return GSI_ERR_ARG;
   for (int i = 0; i < nsteps; ++i) {
     bool stop = false;
-    gsi_status s = c->o.method == GSI_CHEB ? iterate_cheb(c, &stop) : iterate(c, &stop);
+    gsi_status s = iterate_any(c, &stop);
     if (s != GSI_OK) return timeout_check(c, s);
     if (stop) break;
   }
@@ -943,7 +1079,7 @@ gsi_status gsi_solve(gsi_ctx* c, gsi_info* info) {
   if (!c) return GSI_ERR_ARG;
   for (;;) {
     bool stop = false;
-    gsi_status s = c->o.method == GSI_CHEB ? iterate_cheb(c, &stop) : iterate(c, &stop);
+    gsi_status s = iterate_any(c, &stop);
     if (s != GSI_OK) return timeout_check(c, s);
     if (stop) break;
   }

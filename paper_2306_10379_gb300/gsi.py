@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libgsi.so")
 GSI_OK, GSI_ERR_ARG, GSI_ERR_CUDA, GSI_ERR_OOM, GSI_ERR_NOCONV, GSI_ERR_BREAKDOWN, \
     GSI_ERR_NONFINITE, GSI_ERR_TIMEOUT = range(8)
 GSI_CSR, GSI_SELL, GSI_DENSE = 0, 1, 2
-GSI_SD, GSI_CG, GSI_CHEB = 0, 1, 2
+GSI_SD, GSI_CG, GSI_CHEB, GSI_LOBCG = 0, 1, 2, 3
 GSI_PREC_DF64, GSI_PREC_F64, GSI_PREC_MIXED = 0, 1, 2
 PRECISIONS = {"df64": GSI_PREC_DF64, "f64": GSI_PREC_F64, "mixed": GSI_PREC_MIXED}
 KERNEL_CLASSES = ["spmm", "gram", "blockmul", "small", "reduce"]
@@ -428,7 +428,7 @@ class Solver:
         m = _matrix(A, fmt, self._keep)
         o = Opts()
         L.gsi_default_opts(ctypes.byref(o))
-        o.method = {"sd": GSI_SD, "cg": GSI_CG, "cheb": GSI_CHEB}[method]
+        o.method = {"sd": GSI_SD, "cg": GSI_CG, "cheb": GSI_CHEB, "lobcg": GSI_LOBCG}[method]
         o.cheb_degree = int(cheb_degree)
         o.cheb_lo, o.cheb_hi = float(cheb_interval[0]), float(cheb_interval[1])
         o.cheb_scale = float(cheb_scale)

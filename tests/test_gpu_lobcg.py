@@ -1,0 +1,105 @@
+"""The LOBCG comparator (Sec. 6.4, Eq. (def_Vk_LOBPCG)) on the GPU against the
+oracle's lobcg_step / lobcg_solve (the same reading: momentum block P_k,
+Gram-based block orthonormalisation with truncation at 1e-7, explicit
+Q^T A Q), the closed-form spectrum, and App. A's containment of the
+Riemannian step in the LOBCG subspace."""
+import numpy as np
+import pytest
+
+from oracle import gsi_oracle as O
+from paper_2306_10379_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _op(dims):
+    A = I.fd_laplacian(dims)
+    return A, O.csr_operator(A.n, A.rowptr, A.colidx, A.val), I.laplacian_eigenvalues(dims)
+
+
+@pytest.mark.parametrize("precision", ["df64", "f64"])
+@pytest.mark.parametrize("dims,p", [((20, 18), 6), ((16, 15, 14), 16)])
+def test_lobcg_trajectory_matches_oracle(torch_cuda, precision, dims, p):
+    """First 8 iterates: the subspaces agree (sine of the largest principal
+    angle <= 1e-8; the Ritz vectors' signs are arbitrary, the subspaces are
+    not) and so do the partial traces (1e-11 relative)."""
+    from paper_2306_10379_gb300 import gsi
+    A, S, lam = _op(dims)
+    X0 = I.start_block(A.n, p, I.SEED_BASE + 9)
+    ref = O.lobcg_solve(S, X0, tol=0.0, anorm=lam[0], max_iters=8, record=True).history
+    with gsi.Solver(A, p, X0, method="lobcg", tol=1e-8, anorm=lam[0], precision=precision) as s:
+        for k in range(8):
+            s.step(1)
+            X, _ = s.basis(evals=False)
+            Xr = ref[k]
+            # sine of the largest principal angle
+            assert np.linalg.norm(X - Xr @ (Xr.T @ X), 2) <= 1e-8, k
+            tg, tr = np.trace(X.T @ (S @ X)), np.trace(Xr.T @ (S @ Xr))
+            assert abs(tg - tr) <= 1e-11 * abs(tr), k
+
+
+@pytest.mark.parametrize("precision", ["df64", "f64"])
+def test_lobcg_solve_matches_oracle_and_closed_form(torch_cuda, precision):
+    """2D 20 x 18 Laplacian, p = 6: converges to 1e-8, Ritz values within the
+    quadratic residual bound of the closed form, iterations within 2% of the
+    oracle's, and fewer than Riemannian CG's from the same start (as the paper
+    reports for FD matrices)."""
+    from paper_2306_10379_gb300 import gsi
+    dims, p = (20, 18), 6
+    A, S, lam = _op(dims)
+    X0 = I.start_block(A.n, p, I.SEED_BASE + 9)
+    ref = O.lobcg_solve(S, X0, tol=1e-8, anorm=lam[0])
+    with gsi.Solver(A, p, X0, method="lobcg", tol=1e-8, anorm=lam[0], precision=precision) as s:
+        info = s.solve()
+        X, ev = s.basis()
+    with gsi.Solver(A, p, X0, method="cg", tol=1e-8, anorm=lam[0], precision=precision) as s:
+        rcg = s.solve()
+    assert info["converged"] == 1 and ref.converged
+    assert abs(info["iters"] - ref.iters) <= max(2, 0.02 * ref.iters), (info["iters"], ref.iters)
+    gap = lam[p - 1] - lam[p]
+    assert np.max(np.abs(ev - lam[:p])) <= 2 * (1e-8 * lam[0]) ** 2 / gap + 1e-12 * lam[0]
+    assert np.max(np.abs(X.T @ X - np.eye(p))) < 1e-12
+    assert info["iters"] < rcg["iters"]
+    assert info["matvecs"] >= 3 * info["iters"]
+
+
+@pytest.mark.parametrize("precision", ["df64", "f64"])
+def test_lobcg_first_step_contains_the_riemannian_step(torch_cuda, precision):
+    """App. A at k = 0: from the same X_0 the Riemannian step X_0 + t G_0
+    (normalised) lies in span(X_0, G_0), which the first LOBCG step searches,
+    so LOBCG's partial trace is at least Riemannian CG's (and SD's)."""
+    from paper_2306_10379_gb300 import gsi
+    dims, p = (24, 22), 8
+    A, S, lam = _op(dims)
+    X0 = I.start_block(A.n, p, I.SEED_BASE + 13)
+    traces = {}
+    for m in ("lobcg", "cg"):
+        with gsi.Solver(A, p, X0, method=m, tol=1e-8, anorm=lam[0], precision=precision) as s:
+            s.step(1)
+            X, _ = s.basis(evals=False)
+        traces[m] = np.trace(X.T @ (S @ X))
+    assert traces["lobcg"] >= traces["cg"] - 1e-12 * abs(traces["cg"])
+
+
+def test_lobcg_min_problem_and_p64(torch_cuda):
+    """The smallest eigenvalues via -A, and p = 64 (a 192 x 192 Rayleigh-Ritz
+    matrix) on the paper's FD3D grid 35 x 40 x 25 for a few iterations against
+    the oracle."""
+    from paper_2306_10379_gb300 import gsi
+    dims, p = (12, 11), 5
+    A, S, lam = _op(dims)
+    with gsi.Solver(A, p, I.start_block(A.n, p, 3), method="lobcg", which=-1, tol=1e-8, anorm=lam[0]) as s:
+        info = s.solve()
+        _, ev = s.basis()
+    assert info["converged"] == 1
+    assert np.max(np.abs(ev - lam[::-1][:p])) < 1e-10 * lam[0]
+    dims, p = (35, 40, 25), 64
+    A, S, lam = _op(dims)
+    X0 = I.start_block(A.n, p, I.SEED_BASE + 21)
+    ref = O.lobcg_solve(S, X0, tol=0.0, anorm=lam[0], max_iters=3, record=True).history
+    with gsi.Solver(A, p, X0, method="lobcg", tol=1e-8, anorm=lam[0]) as s:
+        for k in range(3):
+            s.step(1)
+            X, _ = s.basis(evals=False)
+            tg, tr = np.trace(X.T @ (S @ X)), np.trace(ref[k].T @ (S @ ref[k]))
+            assert abs(tg - tr) <= 1e-11 * abs(tr), k

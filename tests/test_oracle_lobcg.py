@@ -33,10 +33,10 @@ def test_rcg_iterate_lies_in_the_lobcg_subspace():
         Y = S @ Xk
         C = Xk.T @ Y
         G = Y - Xk @ (0.5 * (C + C.T))
-        Q = O.block_basis([Xk, G, Xm1])
+        Q, _ = O.block_basis([Xk, G, Xm1])
         assert np.max(np.abs(Q.T @ Q - np.eye(Q.shape[1]))) < 1e-12
         assert np.linalg.norm(Xk1 - Q @ (Q.T @ Xk1)) <= 1e-10 * np.linalg.norm(Xk1), k
-        Xl = O.lobcg_step(S, Xk, Xm1)
+        Xl, _ = O.lobcg_step(S, Xk, Xm1)
         assert np.max(np.abs(Xl.T @ Xl - np.eye(p))) < 1e-12
         assert _trace(S, Xl) >= _trace(S, Xk1) - 1e-12 * abs(_trace(S, Xk1)), k
 
@@ -50,7 +50,7 @@ def test_lobcg_first_step_for_p1_is_the_exact_sd_step():
     traj = []
     O.solve(S, x0, O.Options(method="sd", tol=0.0, max_iters=1, anorm=lam[0]),
             callback=lambda k, X, Y, t: traj.append(X.copy()))
-    xl = O.lobcg_step(S, O.orthonormalize(x0))
+    xl, _ = O.lobcg_step(S, O.orthonormalize(x0))
     assert abs(abs(float(xl[:, 0] @ traj[0][:, 0])) - 1.0) < 1e-12
 
 
@@ -71,3 +71,27 @@ def test_lobcg_converges_to_the_closed_form_spectrum():
     assert np.max(np.abs(theta - lam[:p])) <= 2 * (1e-8 * lam[0]) ** 2 / gap + 1e-12 * lam[0]
     rcg = O.solve(S, X0, O.Options(method="cg", tol=1e-8, anorm=lam[0]))
     assert rcg.converged and res.iters < rcg.iters
+
+
+def test_momentum_block_spans_the_same_subspace_as_the_previous_iterate():
+    """The footnote's replacement of X_{k-1}: with P_k the part of X_k outside
+    span(X_{k-1}), span(X_k, G_k, P_k) = span(X_k, G_k, X_{k-1}) (V_1 of X_k
+    in the basis of the previous step is invertible), so a step from either
+    gives the same next iterate (as a subspace and as Ritz values)."""
+    dims, p = (16, 15), 5
+    A, S, lam = _op(dims)
+    X = O.orthonormalize(I.start_block(A.n, p, I.SEED_BASE + 4))
+    Xm1, P = None, None
+    for k in range(4):
+        Xn, Pn = O.lobcg_step(S, X, P)
+        if k >= 1:
+            Y = S @ X
+            G = Y - X @ (X.T @ Y)
+            Qa, _ = O.block_basis([X, G, P])
+            Qb, _ = O.block_basis([X, G, Xm1])
+            assert Qa.shape[1] == Qb.shape[1] == 3 * p
+            assert np.linalg.norm(Qb - Qa @ (Qa.T @ Qb), 2) < 1e-10  # sine of the largest angle
+            Xa, _ = O.lobcg_step(S, X, Xm1)
+            assert np.linalg.norm(Xa - Xn @ (Xn.T @ Xa), 2) < 1e-10
+            assert abs(_trace(S, Xa) - _trace(S, Xn)) < 1e-12 * abs(_trace(S, Xn))
+        Xm1, X, P = X, Xn, Pn
