@@ -75,12 +75,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-baseline", action="store_true", help="skip the native float64 baseline")
     ap.add_argument("--no-forms", action="store_true", help="skip the dense and batched forms")
-    ap.add_argument("--workload", default="fd3d", choices=["fd3d", "dense", "batched", "warm"],
+    ap.add_argument("--workload", default="fd3d", choices=["fd3d", "dense", "batched", "warm", "table"],
                     help="fd3d (default): the 128^3 plain solve with the float64 baseline and the "
                          "forms; dense: mixed precision against float64 on a dense n = 16384, "
                          "p = 128 spectrum; batched: 512 Erdos-Renyi problems in one graph launch "
                          "against the plain solver one problem at a time; warm: learned against "
-                         "random start on a diffusion family")
+                         "random start on a diffusion family; table: RCG and LOBCG on the paper's "
+                         "FD3D matrix (35x40x25), p = 16/32/64, largest and smallest")
     # internal: one CPU-oracle sample in a child process with a thread cap
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--threads", type=int, default=0, help=argparse.SUPPRESS)
@@ -492,6 +493,62 @@ def run_warm(args):
                         "speedup": ms_random / value},
            "clocks": clk, "gpu_launches": launches})
 
+# The paper's FD3D rows of Table "Comparison of LOBCG and Riemannian CG"
+# (seconds / iterations; MATLAB, float64, hardware not stated; iteration
+# counts checked every 50, stopping at ||G_k||_inf / ||G_0||_inf <= 1e-8).
+PAPER_FD3D = {(16, "max"): {"LOBCG(+)": (10, 752), "RCG": (10, 1801)},
+              (16, "min"): {"LOBCG(+)": (8, 652), "RCG": (2, 451)},
+              (32, "max"): {"LOBCG(+)": (16, 552), "RCG": (11, 1051)},
+              (32, "min"): {"LOBCG(+)": (20, 702), "RCG": (40, 3701)},
+              (64, "max"): {"LOBCG(+)": (57, 802), "RCG": (27, 901)},
+              (64, "min"): {"LOBCG(+)": (52, 752), "RCG": (42, 1401)}}
+
+
+def run_table(args):
+    """The FD3D matrix of the paper (3D 7-point Laplacian on 35 x 40 x 25,
+    n = 35,000), p = 16, 32, 64, largest and smallest: Riemannian CG and the
+    LOBCG comparator on the GPU from the same seeded start, both stopping at
+    the paper's criterion ||R_k||_inf / ||R_0||_inf <= 1e-8 (at most 10,000
+    iterations), next to the paper's iteration counts."""
+    import numpy as np
+    import torch
+    from paper_2306_10379_gb300 import build, gsi, inputs as I
+    build.build()
+    dims = (35, 40, 25)
+    A = I.fd_laplacian(dims)
+    lam = I.laplacian_eigenvalues(dims)
+    rows = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = gsi.launch_count()
+    total = 0.0
+    for p in (16, 32, 64):
+        for which in ("max", "min"):
+            X0 = I.start_block(A.n, p, I.SEED_BASE + 100 + p)
+            row = {"p": p, "problem": which, "paper": {k: {"s": v[0], "its": v[1]}
+                                                       for k, v in PAPER_FD3D[(p, which)].items()}}
+            for m in ("cg", "lobcg"):
+                s = gsi.Solver(A, p, X0, method=m, which=1 if which == "max" else -1, tol=1e-8,
+                               anorm=float(lam[0]), max_iters=10000, stop_rule="inf")
+                ms, info = _timed(torch, lambda: s.solve(), 1)
+                _, ev = s.basis()
+                s.close()
+                ref = lam[:p] if which == "max" else lam[::-1][:p]
+                row["RCG" if m == "cg" else "LOBCG(+)"] = {
+                    "ms": ms, "its": info["iters"], "matvecs": info["matvecs"], "converged": info["converged"],
+                    "rel_residual_inf": info["rel_residual_inf"],
+                    "ritz_max_abs_err": float(np.max(np.abs(ev - ref)))}
+                total += ms
+            rows.append(row)
+    clk = clocks.stop()
+    _line(args, "ms to ||R||_inf/||R_0||_inf 1e-8 (RCG and LOBCG, paper's FD3D rows)", total,
+          {"workload": "3D 7-point FD Laplacian 35x40x25 (n=35000), p=16/32/64, largest and smallest, "
+                       "RCG and LOBCG(+) from the same start, stop at ||R||_inf/||R_0||_inf <= 1e-8",
+           "rows": rows, "value_is": "sum of the 12 solves' times"},
+          "df64 blocks, bf16 tensor-core digit products; float64 p x p",
+          {"clocks": clk, "gpu_launches": gsi.launch_count() - l0})
+
+
 def f64_baseline(args, Ad, X0d, lam, iters_to_tol):
     """Native float64 GPU solve of the same workload: F64_TIMED_ITERS
     iterations timed with events after a short warm-up, and the time to
@@ -527,7 +584,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "fd3d":
-        return {"dense": run_dense, "batched": run_batched, "warm": run_warm}[args.workload](args)
+        return {"dense": run_dense, "batched": run_batched, "warm": run_warm,
+                "table": run_table}[args.workload](args)
     import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -107,6 +107,25 @@ typedef struct {
   int32_t cheb_degree;
   double cheb_lo, cheb_hi, cheb_scale;
   double mixed_switch;     /* GSI_PREC_MIXED: residual at which the 7-digit phase starts (1e-5) */
+  /* 0 (default): stop when ||R||_F / anorm <= tol; 1: when ||R_k||_inf /
+   * ||R_0||_inf <= tol (largest row sum of |R|, the criterion of the paper's
+   * Table "Comparison of LOBCG and Riemannian CG"; float32 row sums in df64
+   * mode, within (p + 1) 2^-24 relative). The final check is taken with an
+   * explicit AX either way. */
+  int32_t stop_rule;
+  /* GSI_CHEB: 1 = the filter's bounds follow each Rayleigh-Ritz step (the
+   * practice the paper notes in Sec. 6.2): the unwanted interval is
+   * [cheb_lo, theta_min] and the scaling point theta_max, theta the block's
+   * Ritz values; cheb_lo must be a lower bound of the spectrum, cheb_hi and
+   * cheb_scale are ignored (GSI_ERR_ARG from the step if theta_min <=
+   * cheb_lo). 0 (default) = the fixed interval [cheb_lo, cheb_hi] -- any
+   * upper end, e.g. lambda_{p+k} (the remark after Eq. (optimal_poly)). */
+  int32_t cheb_adaptive;
+  /* GSI_CHEB: guard vectors -- the cheb_guard trailing Ritz pairs (smallest
+   * Ritz values) are left out of the stopping test, 0 <= cheb_guard < p
+   * (default 0). With cheb_adaptive the filter's upper end theta_min then
+   * stays below the wanted eigenvalues. */
+  int32_t cheb_guard;
 } gsi_opts;
 
 typedef struct {
@@ -141,7 +160,8 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
  * Returns GSI_OK (also when converged), or an error status. */
 gsi_status gsi_step(gsi_ctx* ctx, int32_t nsteps, gsi_info* info);
 
-/* Iterate until ||R||_F/anorm <= tol (checked with an explicit AX) or
+/* Iterate until the stopping test of opts.stop_rule holds (checked with an
+ * explicit AX; by default ||R||_F/anorm <= tol) or
  * max_iters; GSI_ERR_NOCONV in the latter case, with info filled and the
  * basis retrievable. */
 gsi_status gsi_solve(gsi_ctx* ctx, gsi_info* info);
@@ -157,6 +177,43 @@ gsi_status gsi_get_basis(gsi_ctx* ctx, double* X, double* evals, int32_t to_devi
 /* Restart from a new start block with the same operator, p and options,
  * reusing the context's device memory (X0 as in gsi_create). */
 gsi_status gsi_reset(gsi_ctx* ctx, const double* X0, int32_t X0_on_device);
+
+/* ---- complex Hermitian A (the footnote to Eq. (phi)) ----------------------
+ * minimise -1/2 Re tr(X^H A X) over X^H X = I: the same Alg. 2 / Alg. 4 on
+ * the complex Grassmannian. The library runs it as the real method on the
+ * realification [[Ar, -Ai], [Ai, Ar]] (2n x 2n) from the realified start
+ * block [[X0r, -X0i], [X0i, X0r]] (2n x 2p): the objective is then twice the
+ * complex one, and the gradient, the Polak-Ribiere beta, the exact step and
+ * the polar factor all commute with the realification, so the real iterates
+ * are the realified complex iterates (the first p columns are [Xr; Xi]). */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t* rowptr;   /* n + 1, 0-based, non-decreasing */
+  const int32_t* colidx;   /* nnz */
+  const double* val;       /* nnz complex values, interleaved (re, im) */
+  int32_t on_device;       /* 0: host arrays, 1: device arrays */
+} gsi_zmatrix;
+
+/* Context for a complex Hermitian A (full storage, Hermitian not checked),
+ * 1 <= p <= 64, n >= 2p; X0 is n x p complex (interleaved re, im, row-major),
+ * host or device by X0_on_device. o: method GSI_SD or GSI_CG (others are
+ * GSI_ERR_ARG); the stopping test is on the complex residual ||R||_F / anorm
+ * when anorm > 0 is given, else ||.||_inf of the realified operator is used.
+ * The inputs are read on the host (device arrays are copied there first) to
+ * build the realified CSR with exact zeros dropped. gsi_step, gsi_solve,
+ * gsi_reset (with a realified 2n x 2p start block), gsi_destroy apply as for
+ * a real context; gsi_info's trace is the complex objective's
+ * tr(X^H A X), its residuals those of the complex iterate (the infinity norm
+ * of the realified rows). */
+gsi_status gsi_create_hermitian(const gsi_zmatrix* A, int32_t p, const double* X0, int32_t X0_on_device,
+                                const gsi_opts* o, void* stream, gsi_ctx** out);
+/* Basis of a Hermitian context: X (n x p complex, interleaved; may be NULL)
+ * the current iterate -- orthonormal, not rotated to Ritz vectors -- and
+ * evals (p, may be NULL) its Ritz values (explicit AX; descending for
+ * which = +1, ascending for -1). to_device: 1 if X and evals are device
+ * pointers. GSI_ERR_ARG for a context not made by gsi_create_hermitian. */
+gsi_status gsi_get_basis_hermitian(gsi_ctx* ctx, double* X, double* evals, int32_t to_device);
 
 /* Subspace tracking (Sec. 1: eigenspaces of a slowly varying matrix, as in
  * self-consistent-field iterations). Replaces the context's operator by A --

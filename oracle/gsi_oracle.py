@@ -19,7 +19,9 @@ paper's D_zeta of Eq. (CG_linesearch_D) after the sign flip), and
 zeta = beta for steepest descent (Eqs. (GTAY)-(GTG)).
 
 Readings of points the paper leaves open:
-  * stopping test ||R||_F / ||A||_2 <= tol, checked every iteration;
+  * stopping test ||R||_F / ||A||_2 <= tol, checked every iteration, or, as
+    an option, the paper's table criterion ||R_k||_inf / ||R_0||_inf <= tol
+    (largest row sum of |R|, Table "Comparison of LOBCG and Riemannian CG");
   * Brent-Dekker root finding on phi'(t) with tolerance 2 eps |t|, at most
     100 evaluations;
   * branches with beta_i <= eps * sum(beta) and, for CG, the concave branches
@@ -41,6 +43,9 @@ Readings of points the paper leaves open:
     orthonormalises by Cholesky) with rank truncation at 1e-7 of each block's
     largest singular value; the Rayleigh-Ritz matrix Q^T A Q is formed
     explicitly (the paper's LOBCG(+));
+  * complex Hermitian A (the footnote to Eq. (phi)): the same steps in
+    complex arithmetic, inner products by their real part, the line-search
+    coefficients the real diagonals of V^H {C, Gamma, Z} V;
   * subspace tracking (the slowly varying operators of Sec. 1): each operator
     of a sequence is solved from the previous one's final iterate, which the
     solve orthonormalises again like any start block; the CG state (direction,
@@ -303,6 +308,7 @@ class Options:
     k_restart: int = 0              # 0 = never
     recompute_every: int = 50
     explicit_ax: bool = False       # RCG(+): explicit AX every iteration
+    stop_rule: str = "fro"          # "fro": ||R||_F / anorm; "inf": ||R_k||_inf / ||R_0||_inf
 
 
 @dataclass
@@ -370,14 +376,15 @@ def solve(A, X0, opts: Options, record=False, callback=None):
         res_inf = float(np.max(np.sum(np.abs(R), axis=1)))
         if res0_inf is None:
             res0_inf = res_inf
-        if rel <= opts.tol or k >= opts.max_iters:
+        crit = rel if opts.stop_rule == "fro" else res_inf / res0_inf
+        if crit <= opts.tol or k >= opts.max_iters:
             if not y_fresh:
                 # the final residual is always taken with an explicit AX
                 Y = spmm(A, X)
                 matvecs += 1
                 y_fresh = True
                 continue
-            converged = rel <= opts.tol
+            converged = crit <= opts.tol
             break
         restarted = False
         if opts.method == "sd" or P is None:
@@ -418,6 +425,88 @@ def solve(A, X0, opts: Options, record=False, callback=None):
         P, R_prev, rr_prev = D, R, rr
         k += 1
     return Result(X, Y, k, matvecs, converged, rel, restarts, history)
+
+
+def solve_hermitian(A, X0, opts: Options):
+    """Alg. 2 / Alg. 4 for a complex Hermitian A (the paper's footnote to
+    Eq. (phi): minimise -1/2 Re tr(X^H A X) over X^H X = I), in complex128,
+    step for step as solve(): transposes become conjugate transposes, inner
+    products take their real part (Re <U, V> = Re tr(U^H V)), B = D^H D is
+    diagonalised by a unitary V and alpha, beta, gamma, zeta are the real
+    diagonals Re diag(V^H {C, Gamma, Z} V) of Hermitian (C, Gamma) or
+    general (Z = D^H R) matrices; Get_Mu, the polar retraction and the AX
+    recursion are unchanged. A: scipy sparse or dense complex, Hermitian;
+    X0: complex n x p."""
+    def herm(M):
+        return 0.5 * (M + M.conj().T)
+
+    def inv_sqrt_h(S):
+        s, U = np.linalg.eigh(herm(S))
+        return (U / np.sqrt(s)) @ U.conj().T
+
+    def rdot(U, V):
+        return float(np.real(np.vdot(U, V)))
+
+    n, p = X0.shape
+    anorm = opts.anorm if opts.anorm > 0 else float(abs(A).sum(axis=1).max())
+    X = np.array(X0, dtype=np.complex128)
+    for _ in range(2):
+        X = X @ inv_sqrt_h(X.conj().T @ X)
+    Y = A @ X
+    matvecs = 1
+    P = R_prev = rr_prev = None
+    restarts = 0
+    y_fresh = True
+    k = 0
+    rel = float("nan")
+    while True:
+        C = herm(X.conj().T @ Y)
+        R = Y - X @ C
+        rr = rdot(R, R)
+        rel = math.sqrt(rr) / anorm
+        if rel <= opts.tol or k >= opts.max_iters:
+            if not y_fresh:
+                Y = A @ X
+                matvecs += 1
+                y_fresh = True
+                continue
+            break
+        restarted = False
+        if opts.method == "sd" or P is None:
+            D = R
+        else:
+            beta_pr = (rr - rdot(R, R_prev)) / rr_prev
+            D = R + beta_pr * (P - X @ (X.conj().T @ P))
+            due = opts.k_restart > 0 and k % opts.k_restart == 0
+            if due or rdot(D, R) <= 0.0:
+                D = R
+                restarted = True
+        restarts += int(restarted)
+        W = A @ D
+        matvecs += 1
+        B = D.conj().T @ D
+        Gam = herm(D.conj().T @ W)
+        Z = B if opts.method == "sd" else D.conj().T @ R
+        beta, V = np.linalg.eigh(herm(B))
+        beta = np.maximum(beta, 0.0)
+        alpha = np.real(np.einsum("ki,kl,li->i", V.conj(), C, V))
+        gamma = np.real(np.einsum("ki,kl,li->i", V.conj(), Gam, V))
+        zeta = np.real(np.einsum("ki,kl,li->i", V.conj(), Z, V))
+        t, _, _, _ = get_mu(alpha, beta, gamma, zeta)
+        Zt = X + t * D
+        M = inv_sqrt_h(Zt.conj().T @ Zt)
+        X = Zt @ M
+        recompute = (opts.explicit_ax or t * math.sqrt(max(beta.max(), 0.0)) < 1e3 * EPS
+                     or (opts.recompute_every > 0 and (k + 1) % opts.recompute_every == 0))
+        if recompute:
+            Y = A @ X
+            matvecs += 1
+        else:
+            Y = (Y + t * W) @ M
+        y_fresh = recompute
+        P, R_prev, rr_prev = D, R, rr
+        k += 1
+    return Result(X, Y, k, matvecs, rel <= opts.tol, rel, restarts)
 
 
 def track(mats, X0, opts: Options, anorms=None):
@@ -490,28 +579,34 @@ def lobcg_step(A, X, W=None):
     return Q @ V, Q[:, w1:] @ V[w1:, :]
 
 
-def lobcg_solve(A, X0, tol=1e-8, anorm=0.0, max_iters=10000, record=False):
+def lobcg_solve(A, X0, tol=1e-8, anorm=0.0, max_iters=10000, record=False, stop_rule="fro"):
     """LOBCG from the orthonormalised X0: (X_{k+1}, P_{k+1}) =
     lobcg_step(A, X_k, P_k) (no momentum block in the first step), with the
-    stopping test of solve(): ||A X_k - X_k C_k||_F <= tol * anorm. record:
-    the Result's history holds each iterate X_k (k >= 1)."""
+    stopping tests of solve(): ||A X_k - X_k C_k||_F <= tol * anorm, or
+    (stop_rule "inf") ||R_k||_inf / ||R_0||_inf <= tol. record: the Result's
+    history holds each iterate X_k (k >= 1)."""
     anorm = anorm if anorm > 0 else anorm_inf(A)
     X = orthonormalize(X0)
     P = None
     k = 0
     hist = []
+    res0_inf = None
     while True:
         Y = spmm(A, X)
         C = gram(X, Y)
         R = residual(X, Y, 0.5 * (C + C.T))
         rel = math.sqrt(float(np.sum(R * R))) / anorm
-        if rel <= tol or k >= max_iters:
+        res_inf = float(np.max(np.sum(np.abs(R), axis=1)))
+        if res0_inf is None:
+            res0_inf = res_inf
+        crit = rel if stop_rule == "fro" else res_inf / res0_inf
+        if crit <= tol or k >= max_iters:
             break
         X, P = lobcg_step(A, X, P)
         if record:
             hist.append(X.copy())
         k += 1
-    return Result(X, Y, k, k + 1, rel <= tol, rel, 0, hist)
+    return Result(X, Y, k, k + 1, crit <= tol, rel, 0, hist)
 
 
 # ---------------------------------------------------------------------------
@@ -534,10 +629,19 @@ def chebyshev_filter(A, X, degree, c, h, scale_at):
     return Z
 
 
-def chebyshev_si(A, X0, degree, lam_p1, lam_n, lam_1, tol=1e-8, anorm=0.0, max_outer=10000):
+def chebyshev_si(A, X0, degree, lam_p1, lam_n, lam_1, tol=1e-8, anorm=0.0, max_outer=10000,
+                 adaptive=False, guard=0):
     """Alg. 1 with p_k = C_d((t - c)/h), c = (lam_{p+1} + lam_n)/2,
     h = (lam_{p+1} - lam_n)/2, scaled at lam_1 (Eq. (optimal_poly)); an
     orthonormalisation and Rayleigh-Ritz after every `degree` matvecs.
+    lam_p1 may be any estimate of the unwanted interval's upper end, e.g.
+    lam_{p+k} (the remark after Eq. (optimal_poly)). adaptive: the bounds
+    follow the Ritz values of each Rayleigh-Ritz step instead (the practice
+    the paper notes in Sec. 6.2): upper end of the unwanted interval the
+    smallest Ritz value of the block, scaling point the largest, lam_n kept
+    as the given lower bound of the spectrum. guard: the trailing Ritz pairs
+    (smallest Ritz values) left out of the stopping test -- guard vectors,
+    which keep the filter's upper end below the wanted eigenvalues.
     Returns (X, theta, outer iterations, matvecs, rel residual)."""
     anorm = anorm if anorm > 0 else anorm_inf(A)
     c = 0.5 * (lam_p1 + lam_n)
@@ -551,10 +655,13 @@ def chebyshev_si(A, X0, degree, lam_p1, lam_n, lam_1, tol=1e-8, anorm=0.0, max_o
         theta, Xr, U = rayleigh_ritz(X, Y)
         Yr = Y @ U
         R = Yr - Xr * theta
-        rel = float(np.linalg.norm(R)) / anorm
+        rel = float(np.linalg.norm(R[:, :R.shape[1] - guard])) / anorm
         X = Xr
         if rel <= tol or outer == max_outer:
             return X, theta, outer, matvecs, rel
+        if adaptive:
+            hi, lam_1 = float(np.min(theta)), float(np.max(theta))
+            c, h = 0.5 * (hi + lam_n), 0.5 * (hi - lam_n)
         Z = chebyshev_filter(A, X, degree, c, h, lam_1)
         matvecs += degree
         Q, _ = np.linalg.qr(Z)

@@ -121,6 +121,7 @@ struct gsi_ctx {
        *W = nullptr, *Xn = nullptr, *Yn = nullptr;
   double* pp = nullptr;  // p x p matrices
   double *Cm, *Bm, *Gm, *Zm, *XXm, *XDm, *Km, *Mm, *Gm2, *out, *dout;
+  double *Tm, *Fm;  // p x p scratch of gsi_get_basis, which no iteration reads
   double* gram_ws = nullptr;
   float2* oz_gram_ws = nullptr;
   void* oz_rhs_ws = nullptr;
@@ -149,6 +150,7 @@ struct gsi_ctx {
   int iters = 0, matvecs = 0, restarts = 0, last_evals = 0;
   bool y_fresh = true, have_prev = false, converged = false;
   double rr_prev = 0.0, res0_inf = -1.0, last_t = 0.0, rel = NAN, rel_inf = NAN;
+  int64_t herm_n = 0;  // > 0: the realification of a complex Hermitian problem of this size
   // per-class timing (CUDA events on the context's stream)
   bool prof = false;
   struct Cls {
@@ -377,6 +379,10 @@ gsi_status orthonormalize(gsi_ctx* c) {
   return GSI_OK;
 }
 
+// The stopped-on quantity: ||R||_F / anorm, or (stop_rule 1) the paper's
+// table criterion ||R||_inf / ||R_0||_inf.
+double crit(const gsi_ctx* c) { return c->o.stop_rule == 1 ? c->rel_inf : c->rel; }
+
 // One iteration; returns GSI_OK and sets *stop when the stopping test holds.
 gsi_status iterate(gsi_ctx* c, bool* stop) {
   const bool cg = c->o.method == GSI_CG;
@@ -413,13 +419,13 @@ gsi_status iterate(gsi_ctx* c, bool* stop) {
       c->have_prev = false;
       continue;
     }
-    if (c->rel <= c->o.tol || c->iters >= c->o.max_iters) {
+    if (crit(c) <= c->o.tol || c->iters >= c->o.max_iters) {
       if (!c->y_fresh) {  // the final residual is always taken with an explicit AX
         GSI_TRY(op_matvec(c, c->X, c->Y));
         c->y_fresh = true;
         continue;
       }
-      c->converged = c->rel <= c->o.tol;
+      c->converged = crit(c) <= c->o.tol;
       *stop = true;
       return GSI_OK;
     }
@@ -574,18 +580,46 @@ gsi_status iterate_cheb(gsi_ctx* c, bool* stop) {
   if (!isfinite(rr)) return GSI_ERR_NONFINITE;
   if (c->res0_inf < 0.0) c->res0_inf = rinf;
   c->rel = sqrt(rr) / c->anorm;
+  if (c->o.cheb_guard > 0) {
+    // guard vectors: only the p - guard largest Ritz pairs enter the test,
+    // from the diagonal of R^T R (column norms) and theta
+    GSI_TRY(op_gram(c, c->R, c->R, true, c->Fm));
+    GSI_TRY(readback(c, c->Fm, p * p));
+    std::vector<double> cn(p);
+    for (int i = 0; i < p; ++i) cn[i] = c->host[i * p + i];
+    GSI_TRY(readback(c, c->XDm, p));
+    std::vector<int> ord(p);
+    for (int i = 0; i < p; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return c->host[a] > c->host[b]; });
+    double rw = 0.0;
+    for (int i = 0; i < p - c->o.cheb_guard; ++i) rw += cn[ord[i]];
+    c->rel = sqrt(rw) / c->anorm;
+  }
   c->rel_inf = c->res0_inf > 0.0 ? rinf / c->res0_inf : 0.0;
   // the Ritz basis is kept in C for fill_info: C <- diag(theta)
   GSI_CUDA_TRY(cudaMemcpyAsync(c->Cm, c->Gm, (size_t)p * p * sizeof(double),
                                cudaMemcpyDeviceToDevice, c->st));
-  if (c->rel <= c->o.tol || c->iters >= c->o.max_iters) {
-    c->converged = c->rel <= c->o.tol;
+  if (crit(c) <= c->o.tol || c->iters >= c->o.max_iters) {
+    c->converged = crit(c) <= c->o.tol;
     *stop = true;
     return GSI_OK;
   }
   // filter: Z_1 = (sigma_1 / h)(A - cI) X, Z_{k+1} = (2 sigma_{k+1} / h)(A - cI) Z_k - sigma_k sigma_{k+1} Z_{k-1}
-  const double cc = 0.5 * (c->o.cheb_hi + c->o.cheb_lo), hh = 0.5 * (c->o.cheb_hi - c->o.cheb_lo);
-  const double e = (c->o.cheb_scale - cc) / hh;
+  double lo = c->o.cheb_lo, hi = c->o.cheb_hi, scale = c->o.cheb_scale;
+  if (c->o.cheb_adaptive) {
+    // Ritz-based bounds: the unwanted interval [cheb_lo, theta_min], scaled at
+    // theta_max (the Ritz values of this step's Rayleigh-Ritz, in XDm)
+    GSI_TRY(readback(c, c->XDm, p));
+    hi = INFINITY;
+    scale = -INFINITY;
+    for (int i = 0; i < p; ++i) {
+      hi = std::min(hi, c->host[i]);
+      scale = std::max(scale, c->host[i]);
+    }
+    if (!(hi > lo)) return GSI_ERR_ARG;
+  }
+  const double cc = 0.5 * (hi + lo), hh = 0.5 * (hi - lo);
+  const double e = (scale - cc) / hh;
   double sigma = 1.0 / e;
   void* bufs[4] = {c->X, c->D, c->P, c->R};
   int ip = 0, ic = 1;
@@ -693,8 +727,8 @@ gsi_status iterate_lobcg(gsi_ctx* c, bool* stop) {
   if (c->res0_inf < 0.0) c->res0_inf = rinf;
   c->rel = sqrt(rr) / c->anorm;
   c->rel_inf = c->res0_inf > 0.0 ? rinf / c->res0_inf : 0.0;
-  if (c->rel <= c->o.tol || c->iters >= c->o.max_iters) {
-    c->converged = c->rel <= c->o.tol;
+  if (crit(c) <= c->o.tol || c->iters >= c->o.max_iters) {
+    c->converged = crit(c) <= c->o.tol;
     *stop = true;
     return GSI_OK;
   }
@@ -755,7 +789,8 @@ void fill_info(gsi_ctx* c, gsi_info* info) {
       cudaStreamSynchronize(c->st) == cudaSuccess) {
     for (int i = 0; i < c->p; ++i) tr += c->host[i * c->p + i];
   }
-  info->trace = c->sign * tr;
+  // the realified objective is twice the complex one
+  info->trace = c->sign * tr * (c->herm_n > 0 ? 0.5 : 1.0);
 }
 
 // the current X as a start block: orthonormalise it, Y = A X, clear the
@@ -920,6 +955,9 @@ gsi_status gsi_default_opts(gsi_opts* o) {
   o->cheb_hi = 0.0;
   o->cheb_scale = 0.0;
   o->mixed_switch = 1e-5;
+  o->stop_rule = 0;
+  o->cheb_adaptive = 0;
+  o->cheb_guard = 0;
   return GSI_OK;
 }
 
@@ -967,13 +1005,15 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
   gsi_opts opts;
   gsi_default_opts(&opts);
   if (o) opts = *o;
-  if (opts.method == GSI_CHEB &&
+  if (opts.method == GSI_CHEB && !opts.cheb_adaptive &&
       (opts.cheb_degree < 1 || !(opts.cheb_hi > opts.cheb_lo) || !(opts.cheb_scale > opts.cheb_hi)))
+    return GSI_ERR_ARG;
+  if (opts.method == GSI_CHEB && (opts.cheb_degree < 1 || opts.cheb_guard < 0 || opts.cheb_guard >= p))
     return GSI_ERR_ARG;
   if (opts.method == GSI_LOBCG && p > 64) return GSI_ERR_ARG;
   if ((opts.method != GSI_SD && opts.method != GSI_CG && opts.method != GSI_CHEB && opts.method != GSI_LOBCG) ||
       (opts.which != 1 && opts.which != -1) ||
-      opts.max_iters < 0 || !(opts.tol >= 0.0) ||
+      opts.max_iters < 0 || !(opts.tol >= 0.0) || (opts.stop_rule != 0 && opts.stop_rule != 1) ||
       (opts.precision != GSI_PREC_DF64 && opts.precision != GSI_PREC_F64 &&
        opts.precision != GSI_PREC_MIXED))
     return GSI_ERR_ARG;
@@ -1005,11 +1045,13 @@ gsi_status gsi_create(const gsi_matrix* A, int32_t p, const double* X0, int32_t 
     c->X = bufs[0]; c->Y = bufs[1]; c->R = bufs[2]; c->Rp = bufs[3];
     c->D = bufs[4]; c->P = bufs[5]; c->W = bufs[6]; c->Xn = bufs[7]; c->Yn = bufs[8];
     const size_t q = (size_t)p * p;
-    CK(dev_alloc(c, (void**)&c->pp, (9 * q + 64) * sizeof(double)));
+    CK(dev_alloc(c, (void**)&c->pp, (11 * q + 64) * sizeof(double)));
     c->Cm = c->pp; c->Bm = c->pp + q; c->Gm = c->pp + 2 * q; c->Zm = c->pp + 3 * q;
     c->XXm = c->pp + 4 * q; c->XDm = c->pp + 5 * q; c->Km = c->pp + 6 * q; c->Mm = c->pp + 7 * q;
     c->Gm2 = c->pp + 8 * q;
-    c->out = c->pp + 9 * q;
+    c->Tm = c->pp + 9 * q;
+    c->Fm = c->pp + 10 * q;
+    c->out = c->pp + 11 * q;
     c->dout = c->out + 16;
     if (c->emu) {
       CK(dev_alloc(c, (void**)&c->oz_gram_ws, oz_gram_scratch_bytes(n, p, p, false)));
@@ -1101,6 +1143,110 @@ gsi_status gsi_device_timeouts(int64_t* count) {
   return s;
 }
 
+gsi_status gsi_create_hermitian(const gsi_zmatrix* A, int32_t p, const double* X0, int32_t X0_on_device,
+                                const gsi_opts* o, void* stream, gsi_ctx** out) {
+  if (!A || !X0 || !out || !A->rowptr || !A->colidx || !A->val || p < 1 || p > 64 || A->n < 1 ||
+      A->n < 2 * (int64_t)p || A->nnz < 0)
+    return GSI_ERR_ARG;
+  if (o && o->method != GSI_SD && o->method != GSI_CG) return GSI_ERR_ARG;
+  const int64_t n = A->n, nnz = A->nnz;
+  std::vector<int64_t> rp(n + 1);
+  std::vector<int32_t> ci(nnz);
+  std::vector<double> va(2 * nnz), x0(2 * (size_t)n * p);
+  cudaMemcpyKind kA = A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  cudaMemcpyKind kX = X0_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  GSI_CUDA_TRY(cudaMemcpy(rp.data(), A->rowptr, (n + 1) * sizeof(int64_t), kA));
+  GSI_CUDA_TRY(cudaMemcpy(ci.data(), A->colidx, nnz * sizeof(int32_t), kA));
+  GSI_CUDA_TRY(cudaMemcpy(va.data(), A->val, 2 * nnz * sizeof(double), kA));
+  GSI_CUDA_TRY(cudaMemcpy(x0.data(), X0, x0.size() * sizeof(double), kX));
+  if (rp[0] != 0 || rp[n] != nnz) return GSI_ERR_ARG;
+  for (int64_t r = 0; r < n; ++r)
+    if (rp[r + 1] < rp[r]) return GSI_ERR_ARG;
+  // [[Ar, -Ai], [Ai, Ar]] (2n x 2n), exact zeros dropped except the diagonal
+  std::vector<int64_t> hrp(2 * n + 1, 0);
+  std::vector<int32_t> hci;
+  std::vector<double> hva;
+  hci.reserve(4 * nnz);
+  hva.reserve(4 * nnz);
+  for (int half = 0; half < 2; ++half)
+    for (int64_t r = 0; r < n; ++r) {
+      const int64_t R = half * n + r;
+      for (int part = 0; part < 2; ++part)  // column block: Re part (cols < n), then Im part
+        for (int64_t k = rp[r]; k < rp[r + 1]; ++k) {
+          const int32_t col = ci[k];
+          if (col < 0 || col >= n) return GSI_ERR_ARG;
+          const double re = va[2 * k], im = va[2 * k + 1];
+          // half 0: row r of [Ar, -Ai]; half 1: row r of [Ai, Ar]
+          const double v = half == 0 ? (part == 0 ? re : -im) : (part == 0 ? im : re);
+          const int64_t C = part * n + col;
+          if (v != 0.0 || C == R) {
+            hci.push_back((int32_t)C);
+            hva.push_back(v);
+          }
+        }
+      hrp[R + 1] = (int64_t)hci.size();
+    }
+  if (2 * n > INT32_MAX) return GSI_ERR_ARG;
+  // [[X0r, -X0i], [X0i, X0r]] (2n x 2p, row-major)
+  std::vector<double> hx(4 * (size_t)n * p);
+  for (int64_t r = 0; r < n; ++r)
+    for (int j = 0; j < p; ++j) {
+      const double re = x0[2 * ((size_t)r * p + j)], im = x0[2 * ((size_t)r * p + j) + 1];
+      hx[(size_t)r * 2 * p + j] = re;
+      hx[(size_t)r * 2 * p + p + j] = -im;
+      hx[(size_t)(n + r) * 2 * p + j] = im;
+      hx[(size_t)(n + r) * 2 * p + p + j] = re;
+    }
+  gsi_opts opts;
+  gsi_default_opts(&opts);
+  if (o) opts = *o;
+  // ||R^||_F = sqrt(2) ||R||_F: the bound scaled alike keeps the test on the complex residual
+  if (opts.anorm > 0) opts.anorm *= sqrt(2.0);
+  gsi_matrix m{};
+  m.fmt = GSI_CSR;
+  m.n = 2 * n;
+  m.nnz = (int64_t)hci.size();
+  m.rowptr = hrp.data();
+  m.colidx = hci.data();
+  m.val = hva.data();
+  m.on_device = 0;
+  GSI_TRY(gsi_create(&m, 2 * p, hx.data(), 0, &opts, stream, out));
+  (*out)->herm_n = n;
+  return GSI_OK;
+}
+
+gsi_status gsi_get_basis_hermitian(gsi_ctx* c, double* X, double* evals, int32_t to_device) {
+  if (!c || c->herm_n <= 0) return GSI_ERR_ARG;
+  const int64_t n = c->herm_n;
+  const int p = c->p / 2;
+  if (evals) {
+    std::vector<double> ev(2 * (size_t)p);
+    GSI_TRY(gsi_get_basis(c, nullptr, ev.data(), 0));
+    std::vector<double> e(p);
+    for (int i = 0; i < p; ++i) e[i] = ev[2 * i];  // each complex Ritz value appears twice
+    if (to_device) {
+      GSI_CUDA_TRY(cudaMemcpy(evals, e.data(), p * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+      memcpy(evals, e.data(), p * sizeof(double));
+    }
+  }
+  if (X) {
+    std::vector<double> xr(4 * (size_t)n * p), xz(2 * (size_t)n * p);
+    GSI_TRY(gsi_get_basis(c, xr.data(), nullptr, 0));
+    for (int64_t r = 0; r < n; ++r)
+      for (int j = 0; j < p; ++j) {
+        xz[2 * ((size_t)r * p + j)] = xr[(size_t)r * 2 * p + j];
+        xz[2 * ((size_t)r * p + j) + 1] = xr[(size_t)(n + r) * 2 * p + j];
+      }
+    if (to_device) {
+      GSI_CUDA_TRY(cudaMemcpy(X, xz.data(), xz.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+      memcpy(X, xz.data(), xz.size() * sizeof(double));
+    }
+  }
+  return GSI_OK;
+}
+
 gsi_status gsi_state_ptrs(gsi_ctx* c, void** X, void** Y) {
   if (!c) return GSI_ERR_ARG;
   if (X) *X = c->X;
@@ -1115,13 +1261,15 @@ gsi_status gsi_get_basis(gsi_ctx* c, double* X, double* evals, int32_t to_device
   cudaMemcpyKind kind = to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const void* src = c->X;
   if (evals) {
-    // Rayleigh-Ritz with an explicit AX: theta in XDm, U in Bm; W and Yn are scratch
+    // Rayleigh-Ritz with an explicit AX: theta in Tm, U in Gm2; W and Yn are
+    // scratch. Only buffers that no later iteration reads are touched (not K
+    // of the CG transport).
     GSI_TRY(op_matvec(c, c->X, c->W));
     c->matvecs--;  // not part of the iteration count
-    GSI_TRY(op_gram(c, c->X, c->W, true, c->Km));
-    GSI_TRY(small_eig(p, c->Km, c->XDm, c->Bm, c->small_ws, c->st));
+    GSI_TRY(op_gram(c, c->X, c->W, true, c->Fm));
+    GSI_TRY(small_eig(p, c->Fm, c->Tm, c->Gm2, c->small_ws, c->st));
     if (X) {
-      GSI_TRY(op_blockmul(c, 1, c->X, c->Bm, 1.0, nullptr, nullptr, 0.0, 0, nullptr, 0.0, nullptr,
+      GSI_TRY(op_blockmul(c, 1, c->X, c->Gm2, 1.0, nullptr, nullptr, 0.0, 0, nullptr, 0.0, nullptr,
                           0.0, c->Yn, false, nullptr));
       src = c->Yn;
     }
@@ -1134,7 +1282,7 @@ gsi_status gsi_get_basis(gsi_ctx* c, double* X, double* evals, int32_t to_device
     GSI_CUDA_TRY(cudaMemcpyAsync(X, src, blk, kind, c->st));
   }
   if (evals) {
-    GSI_CUDA_TRY(cudaMemcpyAsync(c->host, c->XDm, p * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    GSI_CUDA_TRY(cudaMemcpyAsync(c->host, c->Tm, p * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   }
   GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
   prof_harvest(c);

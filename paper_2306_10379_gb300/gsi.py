@@ -30,7 +30,7 @@ EXPORTED = [
     "gsi_retract", "gsi_df_spmm_csr", "gsi_oz_gemm", "gsi_oz_gram", "gsi_reset",
     "gsi_profile_enable", "gsi_profile_read", "gsi_launch_count", "gsi_oz_dense_apply",
     "gsi_oz_gram_noalloc", "gsi_measure_fma_peaks", "gsi_set_operator", "gsi_set_wait_limit",
-    "gsi_device_timeouts",
+    "gsi_device_timeouts", "gsi_create_hermitian", "gsi_get_basis_hermitian",
 ]
 
 
@@ -49,6 +49,11 @@ class Matrix(ctypes.Structure):
                 ("on_device", ctypes.c_int32)]
 
 
+class ZMatrix(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("which", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("anorm", ctypes.c_double), ("max_iters", ctypes.c_int32),
@@ -56,7 +61,8 @@ class Opts(ctypes.Structure):
                 ("explicit_ax", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("cheb_degree", ctypes.c_int32), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("cheb_scale", ctypes.c_double),
-                ("mixed_switch", ctypes.c_double)]
+                ("mixed_switch", ctypes.c_double), ("stop_rule", ctypes.c_int32),
+                ("cheb_adaptive", ctypes.c_int32), ("cheb_guard", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -132,6 +138,9 @@ def _lib():
                               ctypes.c_float, vp, vp, i32, vp],
             "gsi_set_wait_limit": [i32],
             "gsi_set_operator": [vp, ctypes.POINTER(Matrix), dbl],
+            "gsi_create_hermitian": [ctypes.POINTER(ZMatrix), i32, vp, i32, ctypes.POINTER(Opts), vp,
+                                     ctypes.POINTER(vp)],
+            "gsi_get_basis_hermitian": [vp, vp, vp, i32],
             "gsi_device_timeouts": [ctypes.POINTER(i64)],
             "gsi_profile_enable": [vp, i32],
             "gsi_profile_read": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
@@ -383,6 +392,68 @@ class Dense:
         self.n = int(val.shape[0])
 
 
+class HermitianSolver:
+    """gsi_create_hermitian / gsi_step / gsi_solve / gsi_get_basis_hermitian /
+    gsi_destroy for a complex Hermitian A (object with n, rowptr, colidx and
+    complex val, host numpy arrays) and a complex n x p start block."""
+
+    def __init__(self, A, p, X0, method="cg", which=1, tol=1e-8, anorm=0.0, max_iters=10000,
+                 precision="df64", stream=None):
+        L = lib()
+        rp = np.ascontiguousarray(A.rowptr, np.int64)
+        ci = np.ascontiguousarray(A.colidx, np.int32)
+        va = np.ascontiguousarray(np.asarray(A.val, np.complex128).view(np.float64))
+        x0 = np.ascontiguousarray(np.asarray(X0, np.complex128).view(np.float64))
+        self._keep = [rp, ci, va, x0]
+        m = ZMatrix(int(A.n), int(ci.size), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0)
+        o = Opts()
+        L.gsi_default_opts(ctypes.byref(o))
+        o.method = {"sd": GSI_SD, "cg": GSI_CG}[method]
+        o.which = int(which)
+        o.tol = float(tol)
+        o.anorm = float(anorm)
+        o.max_iters = int(max_iters)
+        o.precision = PRECISIONS[precision]
+        self.n, self.p = int(A.n), int(p)
+        ctx = ctypes.c_void_p()
+        _check(L.gsi_create_hermitian(ctypes.byref(m), int(p), ctypes.c_void_p(x0.ctypes.data), 0, ctypes.byref(o),
+                                      _stream(stream), ctypes.byref(ctx)), "gsi_create_hermitian")
+        self._ctx = ctx
+
+    def step(self, nsteps=1):
+        info = Info()
+        _check(lib().gsi_step(self._ctx, int(nsteps), ctypes.byref(info)), "gsi_step")
+        return info.as_dict()
+
+    def solve(self):
+        info = Info()
+        s = lib().gsi_solve(self._ctx, ctypes.byref(info))
+        if s not in (GSI_OK, GSI_ERR_NOCONV):
+            raise GsiError(s, "gsi_solve")
+        return info.as_dict()
+
+    def basis(self, evals=True):
+        """(X, evals): the current complex iterate (n x p, orthonormal) and, with
+        evals, its p Ritz values."""
+        X = np.empty((self.n, self.p), np.complex128)
+        ev = np.empty(self.p) if evals else None
+        _check(lib().gsi_get_basis_hermitian(self._ctx, ctypes.c_void_p(X.ctypes.data),
+                                             ctypes.c_void_p(ev.ctypes.data) if evals else None, 0),
+               "gsi_get_basis_hermitian")
+        return X, ev
+
+    def close(self):
+        if self._ctx:
+            lib().gsi_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 def _matrix(A, fmt, keep):
     """gsi_matrix for A (object with n, rowptr, colidx, val as numpy host arrays
     or torch CUDA tensors; or gsi.Dense); host arrays are kept alive in keep."""
@@ -420,7 +491,7 @@ class Solver:
     def __init__(self, A, p, X0, method="sd", which=1, tol=1e-8, anorm=0.0, max_iters=10000,
                  k_restart=0, recompute_every=50, explicit_ax=False, fmt="csr", precision="df64",
                  cheb_degree=8, cheb_interval=(0.0, 0.0), cheb_scale=0.0, mixed_switch=1e-5,
-                 stream=None):
+                 stop_rule="fro", cheb_adaptive=False, cheb_guard=0, stream=None):
         import torch
         L = lib()
         self._keep = []
@@ -443,6 +514,9 @@ class Solver:
             raise ValueError("precision must be one of " + ", ".join(PRECISIONS))
         o.precision = PRECISIONS[precision]
         o.mixed_switch = float(mixed_switch)
+        o.stop_rule = {"fro": 0, "inf": 1}[stop_rule]
+        o.cheb_adaptive = 1 if cheb_adaptive else 0
+        o.cheb_guard = int(cheb_guard)
         self.precision = precision
         if isinstance(X0, torch.Tensor):
             x0p, x0dev = _dptr(X0, torch.float64, (A.n, p)), 1

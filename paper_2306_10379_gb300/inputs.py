@@ -153,6 +153,73 @@ def fd_laplacian(dims) -> CSR:
     return CSR(n, rowptr, cols[valid].astype(np.int32), vals[valid])
 
 
+class ZCSR:
+    """CSR container of a complex matrix: rowptr int64 (n+1), colidx int32,
+    val complex128."""
+
+    def __init__(self, n: int, rowptr: np.ndarray, colidx: np.ndarray, val: np.ndarray):
+        self.n = int(n)
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self.colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        self.val = np.ascontiguousarray(val, dtype=np.complex128)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def twisted_torus_laplacian(dims, thetas) -> ZCSR:
+    """Complex Hermitian test operator: the periodic FD Laplacian on a grid of
+    shape dims (each d >= 3) whose wrap-around edge along axis a carries the
+    phase exp(i theta_a) (a discrete magnetic Laplacian with flux theta_a
+    through each cycle). Node (i0, i1, ...) is row i0 + d0 (i1 + d1 ...).
+    Row r holds 2 len(dims) on the diagonal and -1 for each neighbour, the
+    neighbour across the wrap edge -exp(+i theta) forwards and -exp(-i theta)
+    backwards; column indices ascending."""
+    dims = tuple(int(d) for d in dims)
+    n = int(np.prod(dims))
+    strides = [1]
+    for d in dims[:-1]:
+        strides.append(strides[-1] * d)
+    rows = [dict() for _ in range(n)]
+    for r in range(n):
+        rows[r][r] = complex(2 * len(dims))
+        rem = r
+        for a, d in enumerate(dims):
+            ia = (rem // strides[a]) % d
+            fwd = r + strides[a] if ia + 1 < d else r - (d - 1) * strides[a]
+            bwd = r - strides[a] if ia > 0 else r + (d - 1) * strides[a]
+            ph_f = np.exp(1j * thetas[a]) if ia + 1 == d else 1.0
+            ph_b = np.exp(-1j * thetas[a]) if ia == 0 else 1.0
+            rows[r][fwd] = rows[r].get(fwd, 0.0) - ph_f
+            rows[r][bwd] = rows[r].get(bwd, 0.0) - ph_b
+    rowptr = np.zeros(n + 1, np.int64)
+    cols, vals = [], []
+    for r in range(n):
+        ks = sorted(rows[r])
+        cols += ks
+        vals += [rows[r][k] for k in ks]
+        rowptr[r + 1] = len(cols)
+    return ZCSR(n, rowptr, np.array(cols), np.array(vals))
+
+
+def twisted_torus_eigenvalues(dims, thetas) -> np.ndarray:
+    """Closed-form spectrum of twisted_torus_laplacian, descending: sums over
+    the axes of 2 - 2 cos((2 pi k + theta_a) / d_a), k = 0..d_a - 1."""
+    total = np.zeros(1)
+    for d, th in zip(dims, thetas):
+        k = np.arange(d)
+        s = 2.0 - 2.0 * np.cos((2.0 * np.pi * k + th) / d)
+        total = (total[:, None] + s[None, :]).ravel()
+    return np.sort(total)[::-1]
+
+
+def complex_start_block(n: int, p: int, seed: int) -> np.ndarray:
+    """n x p complex start block: real and imaginary parts i.i.d. N(0,1)
+    (start_block for the real part, stream 7 for the imaginary part)."""
+    return start_block(n, p, seed) + 1j * gaussian(n * p, seed, stream=7).reshape(n, p)
+
+
 def drifting_laplacians(dims, count: int, eps: float) -> list:
     """A slowly varying sequence for subspace tracking: A_k = L + eps k diag(v),
     k = 0..count-1, L = fd_laplacian(dims) and v the smooth potential

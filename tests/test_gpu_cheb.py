@@ -63,3 +63,28 @@ def test_cheb_rejects_bad_interval(gsi):
     with pytest.raises(gsi.GsiError):
         gsi.Solver(A, 3, I.start_block(A.n, 3, 1), method="cheb", cheb_interval=(1.0, 0.5),
                    cheb_scale=2.0)
+
+
+@pytest.mark.parametrize("precision", ["df64", "f64"])
+def test_cheb_adaptive_matches_oracle(gsi, precision):
+    """Ritz-based bounds (unwanted interval [0, theta_min], scaled at
+    theta_max) with 3 guard vectors: Ritz values after each of the first 4
+    filter steps against the oracle's adaptive run, then the outer iteration
+    count and convergence of the 6 wanted pairs to the closed form."""
+    dims, p, g, d = (20, 18), 9, 3, 8
+    A, lam, S = _problem(dims, p)
+    X0 = I.start_block(A.n, p, 7)
+    with gsi.Solver(A, p, X0, method="cheb", tol=1e-9, anorm=lam[0], precision=precision, cheb_degree=d,
+                    cheb_interval=(0.0, 0.0), cheb_adaptive=True, cheb_guard=g) as s:
+        for k in range(1, 5):
+            s.step(1)
+            _, ev = s.basis()
+            _, th, outer, _, _ = O.chebyshev_si(S, X0, d, 0.0, 0.0, 0.0, tol=0.0, anorm=lam[0], max_outer=k,
+                                                adaptive=True, guard=g)
+            assert np.max(np.abs(ev - th) / np.abs(th)) < 1e-10, k
+        info = s.solve()
+        _, ev = s.basis()
+    _, th, outer, _, _ = O.chebyshev_si(S, X0, d, 0.0, 0.0, 0.0, tol=1e-9, anorm=lam[0], adaptive=True, guard=g)
+    assert info["converged"] == 1
+    assert abs(info["iters"] - outer) <= 1
+    assert np.max(np.abs(ev[:p - g] - lam[:p - g])) < 1e-11 * lam[0]
