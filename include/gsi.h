@@ -305,6 +305,30 @@ gsi_status gsi_csr_to_sell(int64_t n, const int64_t* rowptr, const int32_t* coli
                            int64_t* chunk_ptr, int64_t* chunk_len, int32_t* sell_col,
                            double* sell_val);
 
+/* Diagonal layout of a CSR matrix whose nonzeros lie on at most max_diags
+ * diagonals (finite-difference stencils; host arrays): *ndiag = the number
+ * of distinct offsets col - row, or 0 if there are more than max_diags
+ * (then nothing else is written). offsets (ndiag int64, ascending) and dia
+ * (n x ndiag float64, row-major: dia[r ndiag + d] = A[r, r + offsets[d]], 0
+ * where A has no entry) are written if not NULL. Call with NULL arrays to
+ * size them. */
+gsi_status gsi_csr_to_dia(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* val,
+                          int32_t max_diags, int32_t* ndiag, int64_t* offsets, double* dia);
+
+/* W = A X (Sec. 6.1, one block matvec) for a stencil-shaped A in the
+ * diagonal layout of gsi_csr_to_dia: ndiag <= 8 ascending offsets (a host
+ * array; at most two of them beyond 64 q rows, q the largest window that
+ * fits shared memory for p columns), dia n x ndiag df64 values (2 n ndiag
+ * floats, device), X and W n x p df64 (device), even p <= 64, 16-byte
+ * aligned. A CTA walks
+ * 64-row tiles keeping X's tiles k - q .. k + q in shared memory, filled by
+ * cp.async one tile ahead; the far offsets are read from global memory.
+ * Diagonals are summed in ascending offset order: for sorted CSR rows the
+ * result equals gsi_df_spmm_csr's bit for bit. GSI_ERR_ARG if the shape does
+ * not apply. */
+gsi_status gsi_df_spmm_dia(int64_t n, int32_t ndiag, const int64_t* offsets, const float* dia, int32_t p,
+                           const float* X, float* W, void* stream);
+
 /* W = A X with A in SELL-C-sigma (device arrays from gsi_csr_to_sell).
  * W rows are written at their original (unpermuted) positions. */
 gsi_status gsi_spmm_sell(int64_t n, int64_t nchunks, int32_t C, const int64_t* perm,

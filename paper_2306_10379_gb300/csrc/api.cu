@@ -159,4 +159,23 @@ gsi_status gsi_set_tensor_path(int32_t path) {
 
 int32_t gsi_tensor_path(void) { return tensor_path(); }
 
+gsi_status gsi_df_spmm_dia(int64_t n, int32_t ndiag, const int64_t* offsets, const float* dia, int32_t p,
+                           const float* X, float* W, void* stream) {
+  if (n < 0 || ndiag < 1 || ndiag > DIA_MAXD || !offsets || (n > 0 && (!dia || !X || !W))) return GSI_ERR_ARG;
+  if (((uintptr_t)X & 15) || ((uintptr_t)W & 15) || ((uintptr_t)dia & 7)) return GSI_ERR_ARG;
+  DiaArgs a{};
+  a.n = n;
+  a.p = p;
+  a.nd = ndiag;
+  for (int d = 0; d < ndiag; ++d) {
+    if (offsets[d] <= -n || offsets[d] >= n || (d > 0 && offsets[d] <= offsets[d - 1])) return GSI_ERR_ARG;
+    a.off[d] = (int)offsets[d];
+  }
+  if (!dia_plan(p, ndiag, a.off, &a.q, &a.near_mask, a.far_d, &a.nfar)) return GSI_ERR_ARG;
+  a.val = reinterpret_cast<const float2*>(dia);
+  a.X = reinterpret_cast<const float2*>(X);
+  a.W = reinterpret_cast<float2*>(W);
+  return df_spmm_dia(a, (cudaStream_t)stream);
+}
+
 }  // extern "C"

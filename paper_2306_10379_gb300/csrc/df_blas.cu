@@ -386,4 +386,181 @@ gsi_status df_sum_parts(int nparts, const float2* parts, double* out, cudaStream
   return GSI_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Stencil-shaped operators (every nonzero on one of at most DIA_MAXD
+// diagonals col - row = off[d]): the diagonals' values are stored row-major
+// as df64 (n x nd, zero where A has no entry), and W = A X runs through a
+// shared-memory window. A CTA walks a contiguous range of 64-row tiles; tiles
+// k - q .. k + q of X (and the diagonal values of tile k) sit in a ring of
+// 2q + 2 slots filled by cp.async one tile ahead, so the offsets with
+// |off| <= 64 q are read from shared memory and only the others ("far",
+// at most two) from global memory. For the 3D 7-point stencil on a 128^3
+// grid (offsets 0, +-1, +-128, +-16384, q = 2) an X row is read from L2
+// three times instead of seven. The diagonals are summed in ascending offset
+// order -- the column order of a sorted CSR row -- and the zeros of absent
+// entries add exactly nothing, so the result equals the CSR kernel's bit for
+// bit when the CSR rows are sorted.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16_dia(void* smem, const void* gmem, bool valid) {
+  uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async8_dia(void* smem, const void* gmem, bool valid) {
+  uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+
+template <int NFAR>
+__global__ void __launch_bounds__(DIA_THREADS, 1) df_spmm_dia_kernel(DiaArgs a) {
+  extern __shared__ __align__(16) unsigned char dia_sm[];
+  const int p = a.p, nd = a.nd, q = a.q, NS = 2 * q + 2;
+  const int hp = p / 2;                       // column pairs
+  float2* win = reinterpret_cast<float2*>(dia_sm);                       // NS x DIA_T x p
+  float2* dv = win + (size_t)NS * DIA_T * p;                             // NS x DIA_T x nd
+  const int64_t k0 = (int64_t)blockIdx.x * a.tiles_per_cta;
+  const int64_t k1 = min(a.ntiles, k0 + a.tiles_per_cta);
+  if (k0 >= k1) return;
+  auto slot = [&](int64_t k) { return (int)(((k % NS) + NS) % NS); };
+  // tile k's X rows and (for k in range) its diagonal values into slot(k);
+  // rows outside [0, n) are zero-filled
+  auto load = [&](int64_t k) {
+    float2* xd = win + (size_t)slot(k) * DIA_T * p;
+    const int64_t r0 = k * DIA_T;
+    for (int e = threadIdx.x; e < DIA_T * hp; e += DIA_THREADS) {
+      const int row = e / hp, c2 = e - row * hp;
+      const int64_t R = r0 + row;
+      const bool ok = R >= 0 && R < a.n;
+      cp_async16_dia(xd + row * p + 2 * c2, a.X + (ok ? R * p + 2 * c2 : 0), ok);
+    }
+    float2* vd = dv + (size_t)slot(k) * DIA_T * nd;
+    for (int e = threadIdx.x; e < DIA_T * nd; e += DIA_THREADS) {
+      const int64_t R = r0 + e / nd;
+      const bool ok = R >= 0 && R < a.n;
+      cp_async8_dia(vd + e, a.val + (ok ? r0 * nd + e : 0), ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  for (int64_t k = k0 - q; k <= k0 + q; ++k) load(k);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = lane < hp;
+  constexpr int RPW = DIA_T / (DIA_THREADS / 32);  // rows per warp and tile
+  for (int64_t k = k0; k < k1; ++k) {
+    load(k + q + 1);  // into the slot of tile k - q - 1, free since the last iteration
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    const float2* vk = dv + (size_t)slot(k) * DIA_T * nd;
+    // far diagonals: X rows from global memory, loaded two rows ahead
+    int foff0 = 0, foff1 = 0;
+#pragma unroll
+    for (int d = 0; d < DIA_MAXD; ++d) {
+      if (NFAR > 0 && d == a.far_d[0]) foff0 = a.off[d];
+      if (NFAR > 1 && d == a.far_d[1]) foff1 = a.off[d];
+    }
+    const int64_t nrow = a.n;
+    const float2* Xg = a.X;
+    const int64_t rbase = k * DIA_T + warp;
+    auto far1 = [=](int j, int o) {
+      const int64_t R = rbase + j * (DIA_THREADS / 32);
+      const int64_t col = R + o;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (act && j < RPW && R < nrow && col >= 0 && col < nrow)
+        v = __ldg(reinterpret_cast<const float4*>(Xg + col * p) + lane);
+      return v;
+    };
+    float4 fa0 = make_float4(0.f, 0.f, 0.f, 0.f), fa1 = fa0, fb0 = fa0, fb1 = fa0;
+    if (NFAR > 0) {
+      fa0 = far1(0, foff0);
+      fb0 = far1(1, foff0);
+    }
+    if (NFAR > 1) {
+      fa1 = far1(0, foff1);
+      fb1 = far1(1, foff1);
+    }
+#pragma unroll 1
+    for (int j = 0; j < RPW; ++j) {
+      const float4 fc0 = fa0, fc1 = fa1;
+      fa0 = fb0;
+      fa1 = fb1;
+      if (NFAR > 0) fb0 = far1(j + 2, foff0);
+      if (NFAR > 1) fb1 = far1(j + 2, foff1);
+      const int rr = warp + j * (DIA_THREADS / 32);
+      const int64_t R = k * DIA_T + rr;
+      if (R >= a.n || !act) continue;
+      float h0 = 0.f, e0 = 0.f, h1 = 0.f, e1 = 0.f;
+#pragma unroll
+      for (int d = 0; d < DIA_MAXD; ++d) {  // constant indices keep a.off in parameter space
+        if (d < nd) {
+          const float2 v = vk[rr * nd + d];
+          float4 x;
+          if ((a.near_mask >> d) & 1) {
+            const int src = rr + a.off[d];  // row relative to tile k's first row
+            const int kt = src >= 0 ? src / DIA_T : -((-src + DIA_T - 1) / DIA_T);
+            const int rin = src - kt * DIA_T;
+            x = *reinterpret_cast<const float4*>(win + ((size_t)slot(k + kt) * DIA_T + rin) * p + 2 * lane);
+          } else {
+            x = (NFAR > 1 && a.far_d[1] == d) ? fc1 : fc0;
+          }
+          df_mac(h0, e0, v, make_float2(x.x, x.y));
+          df_mac(h1, e1, v, make_float2(x.z, x.w));
+        }
+      }
+      const float2 r0v = fast_two_sum(h0, e0), r1v = fast_two_sum(h1, e1);
+      reinterpret_cast<float4*>(a.W + R * p)[lane] = make_float4(r0v.x, r0v.y, r1v.x, r1v.y);
+    }
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+size_t dia_smem_bytes(int p, int q, int nd) {
+  return (size_t)(2 * q + 2) * DIA_T * ((size_t)p + nd) * sizeof(float2);
+}
+
+int dia_plan(int p, int nd, const int* off, int* q_out, int* near_mask, int* far_d, int* nfar) {
+  if ((p & 1) || p > 64 || nd < 1 || nd > DIA_MAXD) return 0;
+  // the largest window that fits: 2q + 2 slots of DIA_T rows of X and values
+  int qmax = 0;
+  while (dia_smem_bytes(p, qmax + 1, nd) <= (size_t)DIA_SMEM_MAX) ++qmax;
+  if (qmax < 1) return 0;
+  int q = 1, nf = 0, mask = 0;
+  for (int d = 0; d < nd; ++d) {
+    const int ao = off[d] < 0 ? -off[d] : off[d];
+    if (ao <= DIA_T * qmax) {
+      mask |= 1 << d;
+      q = std::max(q, (ao + DIA_T - 1) / DIA_T);
+    } else {
+      if (nf == DIA_MAXFAR) return 0;
+      far_d[nf++] = d;
+    }
+  }
+  *q_out = q;
+  *near_mask = mask;
+  *nfar = nf;
+  return 1;
+}
+
+gsi_status df_spmm_dia(const DiaArgs& a0, cudaStream_t st) {
+  DiaArgs a = a0;
+  if (a.n <= 0) return GSI_OK;
+  a.ntiles = (a.n + DIA_T - 1) / DIA_T;
+  const int grid = (int)std::min<int64_t>(a.ntiles, sm_count());
+  a.tiles_per_cta = (a.ntiles + grid - 1) / grid;
+  const size_t sm = dia_smem_bytes(a.p, a.q, a.nd);
+  if (a.nfar == 0) {
+    GSI_CUDA_TRY(cudaFuncSetAttribute(df_spmm_dia_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    df_spmm_dia_kernel<0><<<grid, DIA_THREADS, sm, st>>>(a);
+  } else if (a.nfar == 1) {
+    GSI_CUDA_TRY(cudaFuncSetAttribute(df_spmm_dia_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    df_spmm_dia_kernel<1><<<grid, DIA_THREADS, sm, st>>>(a);
+  } else {
+    GSI_CUDA_TRY(cudaFuncSetAttribute(df_spmm_dia_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    df_spmm_dia_kernel<2><<<grid, DIA_THREADS, sm, st>>>(a);
+  }
+  GSI_LAUNCH_CHECK();
+  return GSI_OK;
+}
+
 }  // namespace gsi

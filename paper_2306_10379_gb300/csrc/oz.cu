@@ -579,19 +579,29 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // (b) the 28 digit-pair products, grouped by g = i + j, issued by the
-    // issuing warp (descriptor start addresses advance in 16-byte units)
+    // (b) the 28 digit-pair products, issued by the issuing warp
+    // (descriptor start addresses advance in 16-byte units). For the left
+    // plane i the right planes j = 0 .. 6 - i feed the groups g = i + j,
+    // whose accumulators are adjacent in tensor memory, and the planes are
+    // adjacent in shared memory: one MMA of N = run NC per run of planes
+    // (N <= 256) -- 11 MMAs per 16 columns of K at NC = 64 instead of 28.
+    // Each group still receives i = 0, 1, .. in order (and its sums are
+    // exact integers in any order).
     if (issuer) {
       if (lane == 0) {
         const uint64_t da = tc_desc(abase, K16), db = tc_desc(bbase, K16);
         const uint32_t ap4 = aplane >> 4, bp4 = bplane >> 4;
+        const uint32_t idesc0 = idesc & ~(0x3Fu << 17);
+        const int maxrun = 256 / NC;
 #pragma unroll
-        for (int g = 0; g < ND; ++g)
-#pragma unroll
-          for (int i = 0; i <= g; ++i)
+        for (int i = 0; i < ND; ++i)
+          for (int j0 = 0; j0 < ND - i; j0 += maxrun) {
+            const int run = min(maxrun, ND - i - j0);
+            const uint32_t idn = idesc0 | ((uint32_t)((NC * run) >> 3) << 17);
             for (int ks = 0; ks < K16 / 16; ++ks)
-              tc_mma(tmem + (uint32_t)(g * NC), da + i * ap4 + ks * 16, db + (g - i) * bp4 + ks * 16, idesc,
+              tc_mma(tmem + (uint32_t)((i + j0) * NC), da + i * ap4 + ks * 16, db + j0 * bp4 + ks * 16, idn,
                      (i > 0 || ks > 0) ? 1u : 0u);
+          }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
                      : "memory");
       }
@@ -1162,14 +1172,23 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
           const uint32_t ab = dbase + buf * TG_DBUF, bb = SYM ? ab : ab + 7 * plane;
           const uint64_t da = tc_desc(ab, SK), db = tc_desc(bb, SK);
           const uint32_t acc0 = s > 0 ? 1u : 0u;
+          // V's planes j0 .. j0 + run - 1 are adjacent in shared memory and so
+          // are their accumulator blocks 2m + j0 .. in tensor memory: one
+          // MMA of N = 64 run per run of up to 4 planes (6 MMAs per 16 rows
+          // instead of 16 of N = 64; the per-instruction cost dominates at
+          // N = 64)
+          const uint32_t idesc0 = idesc & ~(0x3Fu << 17);
 #pragma unroll
           for (int m = 0; m < 4; ++m)
 #pragma unroll
-            for (int j = 0; j < ND - 2 * m; ++j)
+            for (int j0 = 0; j0 < ND - 2 * m; j0 += 4) {
+              const int run = (ND - 2 * m - j0) < 4 ? (ND - 2 * m - j0) : 4;
+              const uint32_t idn = idesc0 | ((uint32_t)((64 * run) >> 3) << 17);
 #pragma unroll
               for (int ks = 0; ks < SK / 16; ++ks)
-                tc_mma(tmem + (uint32_t)((2 * m + j) * 64), da + ((2 * m * plane + ks * 256) >> 4),
-                       db + ((j * plane + ks * 256) >> 4), idesc, (m > 0 || ks > 0) ? 1u : acc0);
+                tc_mma(tmem + (uint32_t)((2 * m + j0) * 64), da + ((2 * m * plane + ks * 256) >> 4),
+                       db + ((j0 * plane + ks * 256) >> 4), idn, (m > 0 || ks > 0) ? 1u : acc0);
+            }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            buf ? mb1 : mb0)
                        : "memory");

@@ -61,6 +61,30 @@ gsi_status oz_set_wait_limit(int limit);
 // enqueue a copy of the process-wide timeout count into host_dst (pinned)
 gsi_status oz_timeouts_async(int* host_dst, cudaStream_t st);
 
+// Stencil-shaped operators: at most DIA_MAXD diagonals (df_blas.cu)
+constexpr int DIA_T = 64;            // rows per tile of the shared-memory window
+constexpr int DIA_MAXD = 8;          // diagonals stored
+constexpr int DIA_MAXFAR = 2;        // diagonals read from global memory
+constexpr int DIA_THREADS = 512;
+constexpr int DIA_SMEM_MAX = 220 * 1024;
+struct DiaArgs {
+  int64_t n;
+  int p, nd, q;                      // q: the window holds tiles k - q .. k + q
+  int off[DIA_MAXD];                 // col - row of each diagonal, ascending
+  int near_mask;                     // bit d: diagonal d read from the window
+  int far_d[DIA_MAXFAR];             // the other diagonals
+  int nfar;
+  const float2* val;                 // n x nd df64 values, row-major
+  const float2* X;
+  float2* W;
+  int64_t ntiles, tiles_per_cta;     // set by df_spmm_dia
+};
+size_t dia_smem_bytes(int p, int q, int nd);
+// window geometry for p columns and the diagonals off[0..nd): 1 if the
+// staged kernel applies (even p <= 64, at most DIA_MAXFAR far diagonals)
+int dia_plan(int p, int nd, const int* off, int* q, int* near_mask, int* far_d, int* nfar);
+gsi_status df_spmm_dia(const DiaArgs& a, cudaStream_t st);
+
 // df64 block helpers (df_blas.cu)
 gsi_status df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);
 gsi_status df_to_f64(int64_t count, const float2* x, double* y, cudaStream_t st);

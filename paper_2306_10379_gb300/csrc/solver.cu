@@ -107,6 +107,9 @@ struct gsi_ctx {
   int32_t* colidx = nullptr;
   double* val = nullptr;    // float64 values (native mode and Rayleigh-Ritz)
   float2* vdf = nullptr;    // df64 values
+  float2* dia_val = nullptr;  // stencil-shaped A: df64 values by row and diagonal
+  DiaArgs dia{};              // its diagonals and shared-memory window
+  bool use_dia = false;
   int C = 32;
   int64_t nchunks = 0;
   int64_t* perm = nullptr;
@@ -261,6 +264,12 @@ gsi_status op_matvec(gsi_ctx* c, const void* in, void* outp, bool accurate = tru
                               c->sdf, c->p, (const float2*)in, (float2*)outp, c->st)
                : spmm_sell(c->n, c->nchunks, c->C, c->perm, c->chunk_ptr, c->chunk_len, c->scol,
                            c->sval, c->p, (const double*)in, (double*)outp, c->st);
+  } else if (c->use_dia && ((uintptr_t)in & 15) == 0 && ((uintptr_t)outp & 15) == 0) {
+    bytes = 8.0 * (double)c->dia.nd * c->n + 2 * blk_bytes(c);
+    DiaArgs a = c->dia;
+    a.X = (const float2*)in;
+    a.W = (float2*)outp;
+    s = df_spmm_dia(a, c->st);
   } else {
     bytes = 12.0 * (double)c->nnz + 8.0 * (c->n + 1) + 2 * blk_bytes(c);
     s = c->emu ? df_spmm_csr(c->n, c->rowptr, c->colidx, c->vdf, c->p, (const float2*)in,
@@ -836,6 +845,44 @@ gsi_status realloc_dev(gsi_ctx* c, void** p, size_t bytes) {
   return dev_alloc(c, p, bytes);
 }
 
+// Stencil-shaped CSR operators (every nonzero on one of at most DIA_MAXD
+// diagonals, p even <= 64, df64 mode): the diagonal layout for the staged
+// SpMM. GSI_SPMM_DIA=0 in the environment keeps the CSR kernel (for
+// comparisons).
+gsi_status setup_dia(gsi_ctx* c, const gsi_matrix* A) {
+  c->use_dia = false;
+  const char* env = getenv("GSI_SPMM_DIA");
+  if (!c->emu || c->fmt != GSI_CSR || (c->p & 1) || c->p > 64 || (env && env[0] == '0')) return GSI_OK;
+  const int64_t n = c->n, nnz = c->nnz;
+  cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  std::vector<int64_t> rp(n + 1);
+  std::vector<int32_t> ci(nnz);
+  GSI_CUDA_TRY(cudaMemcpy(rp.data(), A->rowptr, (n + 1) * sizeof(int64_t), kind));
+  GSI_CUDA_TRY(cudaMemcpy(ci.data(), A->colidx, nnz * sizeof(int32_t), kind));
+  int32_t nd = 0;
+  int64_t offs[DIA_MAXD];
+  GSI_TRY(gsi_csr_to_dia(n, rp.data(), ci.data(), nullptr, DIA_MAXD, &nd, offs, nullptr));
+  if (nd < 1) return GSI_OK;
+  DiaArgs a{};
+  a.n = n;
+  a.p = c->p;
+  a.nd = nd;
+  for (int d = 0; d < nd; ++d) a.off[d] = (int)offs[d];
+  if (!dia_plan(c->p, nd, a.off, &a.q, &a.near_mask, a.far_d, &a.nfar)) return GSI_OK;
+  std::vector<double> hv(nnz), dv((size_t)n * nd);
+  GSI_CUDA_TRY(cudaMemcpy(hv.data(), A->val, nnz * sizeof(double), kind));
+  GSI_TRY(gsi_csr_to_dia(n, rp.data(), ci.data(), hv.data(), DIA_MAXD, &nd, offs, dv.data()));
+  std::vector<float2> df(dv.size());
+  for (size_t e = 0; e < dv.size(); ++e) df[e] = df_from_double(c->sign * dv[e]);
+  GSI_TRY(realloc_dev(c, (void**)&c->dia_val, df.size() * sizeof(float2)));
+  GSI_CUDA_TRY(cudaMemcpyAsync(c->dia_val, df.data(), df.size() * sizeof(float2), cudaMemcpyHostToDevice, c->st));
+  GSI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  a.val = c->dia_val;
+  c->dia = a;
+  c->use_dia = true;
+  return GSI_OK;
+}
+
 // Copy the operator A into the context's device memory (sign applied for
 // which = -1), with its df64 copy and, for GSI_SELL, its SELL-C-sigma layout.
 // Buffers are (re)allocated when missing or when A's sizes differ from the
@@ -877,6 +924,7 @@ gsi_status upload_operator(gsi_ctx* c, const gsi_matrix* A) {
     GSI_CUDA_TRY(cudaGetLastError());
   }
   if (c->emu) GSI_TRY(df_from_f64(c->nnz, c->val, c->vdf, c->st));
+  GSI_TRY(setup_dia(c, A));
   if (c->fmt == GSI_SELL) {
     c->C = A->sell_C > 0 ? A->sell_C : 32;
     int sigma = A->sell_sigma > 0 ? A->sell_sigma : 32;

@@ -30,7 +30,8 @@ EXPORTED = [
     "gsi_retract", "gsi_df_spmm_csr", "gsi_oz_gemm", "gsi_oz_gram", "gsi_reset",
     "gsi_profile_enable", "gsi_profile_read", "gsi_launch_count", "gsi_oz_dense_apply",
     "gsi_oz_gram_noalloc", "gsi_measure_fma_peaks", "gsi_set_operator", "gsi_set_wait_limit",
-    "gsi_device_timeouts", "gsi_create_hermitian", "gsi_get_basis_hermitian",
+    "gsi_device_timeouts", "gsi_create_hermitian", "gsi_get_basis_hermitian", "gsi_csr_to_dia",
+    "gsi_df_spmm_dia",
 ]
 
 
@@ -137,6 +138,8 @@ def _lib():
             "gsi_gemm_bf16": [i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, ctypes.c_float,
                               ctypes.c_float, vp, vp, i32, vp],
             "gsi_set_wait_limit": [i32],
+            "gsi_csr_to_dia": [i64, vp, vp, vp, i32, ctypes.POINTER(i32), vp, vp],
+            "gsi_df_spmm_dia": [i64, i32, vp, vp, i32, vp, vp, vp],
             "gsi_set_operator": [vp, ctypes.POINTER(Matrix), dbl],
             "gsi_create_hermitian": [ctypes.POINTER(ZMatrix), i32, vp, i32, ctypes.POINTER(Opts), vp,
                                      ctypes.POINTER(vp)],
@@ -340,6 +343,35 @@ def df_spmm_csr(rowptr, colidx, val_df, X_df, W_df, stream=None):
     _check(lib().gsi_df_spmm_csr(n, _dptr(rowptr, torch.int64), _dptr(colidx, torch.int32),
                                  _dptr(val_df, f), p, _dptr(X_df, f), _dptr(W_df, f, (n, p, 2)),
                                  _stream(stream)), "gsi_df_spmm_csr")
+
+
+def csr_to_dia(n, rowptr, colidx, val, max_diags=8):
+    """Host diagonal layout: (offsets int64, dia n x ndiag float64), or None
+    when the nonzeros lie on more than max_diags diagonals."""
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    colidx = np.ascontiguousarray(colidx, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    nd = ctypes.c_int32()
+    _check(lib().gsi_csr_to_dia(n, rowptr.ctypes.data, colidx.ctypes.data, None, max_diags, ctypes.byref(nd),
+                                None, None), "gsi_csr_to_dia")
+    if nd.value == 0:
+        return None
+    off = np.empty(nd.value, np.int64)
+    dia = np.empty((n, nd.value), np.float64)
+    _check(lib().gsi_csr_to_dia(n, rowptr.ctypes.data, colidx.ctypes.data, val.ctypes.data, max_diags,
+                                ctypes.byref(nd), off.ctypes.data, dia.ctypes.data), "gsi_csr_to_dia")
+    return off, dia
+
+
+def df_spmm_dia(offsets, dia_df, X_df, W_df, stream=None):
+    """W = A X for the diagonal layout (offsets host int64, dia_df a device df64
+    tensor n x ndiag x 2)."""
+    import torch
+    n, p = X_df.shape[0], X_df.shape[1]
+    off = np.ascontiguousarray(offsets, np.int64)
+    f = torch.float32
+    _check(lib().gsi_df_spmm_dia(n, int(off.size), ctypes.c_void_p(off.ctypes.data), _dptr(dia_df, f), p,
+                                 _dptr(X_df, f), _dptr(W_df, f, (n, p, 2)), _stream(stream)), "gsi_df_spmm_dia")
 
 
 def oz_gemm(U0, M0, out, s0=1.0, U1=None, M1=None, s1=0.0, E=(), c=(), stream=None):

@@ -57,3 +57,22 @@ def test_host_only_calls():
     perm, cptr, clen, scol, sval = gsi.csr_to_sell(3, rp, ci, va, C=2, sigma=2)
     assert perm.tolist() == [0, 1, 2, -1]
     assert clen.tolist() == [2, 0]
+
+
+def test_csr_to_dia_host_layout():
+    """The host diagonal layout: offsets of a 3D stencil, values by row and
+    diagonal with zeros where the CSR has no entry, and None beyond max_diags."""
+    import numpy as np
+    from paper_2306_10379_gb300 import gsi, inputs as I
+    A = I.fd_laplacian((5, 4, 3))
+    off, dia = gsi.csr_to_dia(A.n, A.rowptr, A.colidx, A.val)
+    assert off.tolist() == [-20, -5, -1, 0, 1, 5, 20]
+    dense = np.zeros((A.n, A.n))
+    for r in range(A.n):
+        for k in range(A.rowptr[r], A.rowptr[r + 1]):
+            dense[r, A.colidx[k]] = A.val[k]
+    for r in range(A.n):
+        for d, o in enumerate(off):
+            c = r + o
+            assert dia[r, d] == (dense[r, c] if 0 <= c < A.n else 0.0)
+    assert gsi.csr_to_dia(A.n, A.rowptr, A.colidx, A.val, max_diags=5) is None
