@@ -400,7 +400,11 @@ gsi_status df_sum_parts(int nparts, const float2* parts, double* out, cudaStream
 // three times instead of seven. The diagonals are summed in ascending offset
 // order -- the column order of a sorted CSR row -- and the zeros of absent
 // entries add exactly nothing, so the result equals the CSR kernel's bit for
-// bit when the CSR rows are sorted.
+// bit when the CSR rows are sorted. Measured at 128^3 it is slower than the
+// CSR kernel (p = 64: 1.59 against 1.02 ms; p = 8: 1.35 against 0.14 ms):
+// one CTA per SM with serial per-row accumulation leaves a per-tile latency
+// floor, and with contiguous tile ranges per CTA the far-diagonal rows are
+// not in L2 when they are read. The solver uses it only on request.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16_dia(void* smem, const void* gmem, bool valid) {
   uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -451,7 +455,8 @@ __global__ void __launch_bounds__(DIA_THREADS, 1) df_spmm_dia_kernel(DiaArgs a) 
     load(k + q + 1);  // into the slot of tile k - q - 1, free since the last iteration
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
-    const float2* vk = dv + (size_t)slot(k) * DIA_T * nd;
+    const int s0 = slot(k);  // the window's tiles k + kt sit in slots s0 + kt (mod NS), |kt| <= q < NS
+    const float2* vk = dv + (size_t)s0 * DIA_T * nd;
     // far diagonals: X rows from global memory, loaded two rows ahead
     int foff0 = 0, foff1 = 0;
 #pragma unroll
@@ -499,7 +504,10 @@ __global__ void __launch_bounds__(DIA_THREADS, 1) df_spmm_dia_kernel(DiaArgs a) 
             const int src = rr + a.off[d];  // row relative to tile k's first row
             const int kt = src >= 0 ? src / DIA_T : -((-src + DIA_T - 1) / DIA_T);
             const int rin = src - kt * DIA_T;
-            x = *reinterpret_cast<const float4*>(win + ((size_t)slot(k + kt) * DIA_T + rin) * p + 2 * lane);
+            int sk = s0 + kt;
+            sk += sk < 0 ? NS : 0;
+            sk -= sk >= NS ? NS : 0;
+            x = *reinterpret_cast<const float4*>(win + ((size_t)sk * DIA_T + rin) * p + 2 * lane);
           } else {
             x = (NFAR > 1 && a.far_d[1] == d) ? fc1 : fc0;
           }

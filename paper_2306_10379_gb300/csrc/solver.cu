@@ -847,12 +847,14 @@ gsi_status realloc_dev(gsi_ctx* c, void** p, size_t bytes) {
 
 // Stencil-shaped CSR operators (every nonzero on one of at most DIA_MAXD
 // diagonals, p even <= 64, df64 mode): the diagonal layout for the staged
-// SpMM. GSI_SPMM_DIA=0 in the environment keeps the CSR kernel (for
-// comparisons).
+// SpMM, used when GSI_SPMM_DIA=1 in the environment at creation. Not the
+// default: at 128^3 it measured slower than the CSR kernel at every p
+// (p = 64: 1.59 against 1.02 ms), bound by one CTA per SM and far-diagonal
+// rows that leave L2 before their reuse.
 gsi_status setup_dia(gsi_ctx* c, const gsi_matrix* A) {
   c->use_dia = false;
   const char* env = getenv("GSI_SPMM_DIA");
-  if (!c->emu || c->fmt != GSI_CSR || (c->p & 1) || c->p > 64 || (env && env[0] == '0')) return GSI_OK;
+  if (!c->emu || c->fmt != GSI_CSR || (c->p & 1) || c->p > 64 || !(env && env[0] == '1')) return GSI_OK;
   const int64_t n = c->n, nnz = c->nnz;
   cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
   std::vector<int64_t> rp(n + 1);

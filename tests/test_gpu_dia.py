@@ -67,10 +67,9 @@ def test_dia_rejects_unsupported_shapes(G):
 
 
 def test_solver_takes_the_staged_kernel(G):
-    """A 3D Laplacian solve through the staged SpMM (the default for stencil
-    operators) and through the CSR kernel (GSI_SPMM_DIA=0 at creation):
-    identical trajectories (the two SpMMs are bit-identical), identical
-    results."""
+    """A 3D Laplacian solve through the staged SpMM (GSI_SPMM_DIA=1 at
+    creation) and through the CSR kernel (the default): identical
+    trajectories (the two SpMMs are bit-identical), identical results."""
     torch, gsi = G
     dims, p = (24, 22, 20), 16
     A = I.fd_laplacian(dims)
