@@ -41,12 +41,12 @@ GPU_ITERS_TO_TOL = {("cg", 128, 64): 4953}
 # n = 512,000 (80^3), p = 64, scaled to the bench size by the rows processed
 # (traffic grows in proportion); averaged over one iteration's launches of the
 # class (2 U^T U + 3 U^T V Grams; 2 fused retractions + 2 products with
-# elementwise terms). None where the kernel changed after the capture.
+# elementwise terms; the CSR SpMM). None where a kernel changed after its
+# capture.
 NCU_TRAFFIC = {
-    "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.249e6 + 3.685e6) + 3 * (524.391e6 + 3.592e6)) / 5},
-    "blockmul": {"n": 512000, "p": 64, "bytes": ((524.523e6 + 226.326e6) + (524.506e6 + 226.865e6)
-                                                  + 2 * (786.842e6 + 240.490e6)) / 4},
-    "spmm": None,
+    "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.319e6 + 3.630e6) + 3 * (524.560e6 + 3.676e6)) / 5},
+    "blockmul": {"n": 512000, "p": 64, "bytes": (2 * (524.473e6 + 224.485e6) + 2 * (786.623e6 + 238.002e6)) / 4},
+    "spmm": {"n": 512000, "p": 64, "bytes": 308.8e6 + 229.4e6},
 }
 TRAFFIC_SOURCE = "one-kernel ncu captures at 80^3 (n = 512,000, p = 64), scaled by rows"
 

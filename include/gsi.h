@@ -432,11 +432,14 @@ gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, 
                                int32_t sym, double* G, void* stream);
 
 /* Which tensor-core kernels the digit-split products use: 0 (default) and 2
- * the tcgen05 kernels wherever they apply (all products with p, q <= 64),
- * 1 the mma.sync kernels everywhere. Block products are identical on both
+ * the tcgen05 kernels wherever they apply (7-digit Grams of any p, q <= 128
+ * and the 7-digit dense apply, one CTA per 64 x 64 output block; 7-digit
+ * block products with p <= 64), 1 the mma.sync kernels everywhere (they
+ * also serve the 3-digit products and block products with p > 64). Block products are identical on both
  * (same digits, exact integer digit-pair sums, same combination order).
  * Grams agree to float64-class accuracy but not bit for bit: the tcgen05
- * Gram takes its column exponents over 256-row (U == V) or 160-row chunks,
+ * Gram takes its column exponents over 256-row (U == V, p <= 64) or 160-row
+ * chunks,
  * the mma.sync Gram over 64-row chunks. The switch exists to compare them.
  * Process-wide; the environment variable GSI_TENSOR_PATH=mma or =tcgen05
  * selects 1 or 2 before the first product. */

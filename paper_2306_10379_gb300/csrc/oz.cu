@@ -1016,8 +1016,25 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
 template <bool SYM>
 __global__ void __launch_bounds__(TG_THREADS, 1)
 oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
-                  int vec16, float2* part) {
+                  int vec16, float2* part, int nbj, int tri) {
   using Geo = TgGeom<SYM>;
+  // the 64 x 64 output block of this CTA: U's columns 64 bi .., V's 64 bj ..
+  // (blockIdx.y over the nbi x nbj blocks, or with tri over the upper
+  // triangle bi <= bj row by row)
+  int bi = 0, bj = (int)blockIdx.y;
+  if (tri) {
+    int y = (int)blockIdx.y;
+    while (y >= nbj - bi) {
+      y -= nbj - bi;
+      ++bi;
+    }
+    bj = bi + y;
+  } else {
+    bi = (int)blockIdx.y / nbj;
+    bj = (int)blockIdx.y - bi * nbj;
+  }
+  const int cu0 = 64 * bi, cv0 = 64 * bj;
+  const int wu = min(64, p - cu0), wv = min(64, q - cv0);  // live columns of the block
   constexpr int EC = Geo::EC, SK = Geo::SK, NSUB = EC / SK, RAWR = Geo::RAWR, NG = Geo::NG;
   constexpr uint32_t TG_DBUF = Geo::DBUF;
   constexpr uint32_t plane = 64u * SK * 2;  // one digit plane: 64 columns x SK rows, bf16
@@ -1081,8 +1098,8 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
         const bool isv = !SYM && row >= EC;
         const int64_t R = r0 + (isv ? row - EC : row);
         const int ld = isv ? q : p;
-        const float2* src = isv ? V : U;
-        const bool ok = R < n && c < ld;
+        const float2* src = (isv ? V + cv0 : U + cu0);
+        const bool ok = R < n && c < (isv ? wv : wu);
         cp_async16(raw + row * TG_RS + c, src + (ok ? R * ld + c : 0), ok);
       }
     } else {
@@ -1091,8 +1108,8 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
         const bool isv = !SYM && row >= EC;
         const int64_t R = r0 + (isv ? row - EC : row);
         const int ld = isv ? q : p;
-        const float2* src = isv ? V : U;
-        const bool ok = R < n && c < ld;
+        const float2* src = (isv ? V + cv0 : U + cu0);
+        const bool ok = R < n && c < (isv ? wv : wu);
         cp_async8(raw + row * TG_RS + c, src + (ok ? R * ld + c : 0), ok);
       }
     }
@@ -1263,7 +1280,7 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   }
   __syncthreads();
   if (!issuer && top) {
-    float2* out = part + (size_t)blockIdx.x * 4096;
+    float2* out = part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * 4096;
 #pragma unroll
     for (int e = 0; e < 16; ++e) out[arow * 64 + cb + e] = df_add(res[e], st[arow * 65 + cb + e]);
   }
@@ -1298,6 +1315,25 @@ __global__ void oz_gram_reduce_kernel(int p, int q, int nsplit, int nblk, int sy
   }
   float2 s = make_float2(0.f, 0.f);
   // unrolled so that several partials are in flight at once (same order)
+#pragma unroll 8
+  for (int k = 0; k < nsplit; ++k) s = df_add(s, part[((size_t)k * nblk + b) * 4096 + ii * 64 + jj]);
+  G[e] = df_to_double(s);
+}
+
+// The same for a symmetric Gram whose upper-triangle blocks (bi <= bj, row by
+// row) were computed in full by the tcgen05 kernel: entry (i, j) is read
+// from the upper triangle, so G is exactly symmetric.
+__global__ void oz_gram_reduce_tri_kernel(int p, int nsplit, int nblk, int nbj, const float2* part, double* G) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p * p) return;
+  const int i = e / p, j = e - i * p;
+  const int si = min(i, j), sj = max(i, j);
+  const int bi = si / 64, bj = sj / 64;
+  int b = 0;
+  for (int r = 0; r < bi; ++r) b += nbj - r;
+  b += bj - bi;
+  const int ii = si - bi * 64, jj = sj - bj * 64;
+  float2 s = make_float2(0.f, 0.f);
 #pragma unroll 8
   for (int k = 0; k < nsplit; ++k) s = df_add(s, part[((size_t)k * nblk + b) * 4096 + ii * 64 + jj]);
   G[e] = df_to_double(s);
@@ -1458,14 +1494,25 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
   int ns = oz_gram_splits(n, p, q, sym);
   if (reserve_sms > 0) ns = std::max(1, std::min(ns, (sm_count() - reserve_sms) / nblk));
   const int tp = tensor_path();
+  // 16-byte copies need even row lengths and 16-byte aligned bases
+  const bool vec16 = ((p | q) & 1) == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)V & 15) == 0;
+  bool tri = false;  // symmetric Gram from full upper-triangle blocks
   if (nd == ND && p <= 64 && q <= 64 && tp != 1) {
-    // one 64 x 64 output block; every partial entry is written. 16-byte
-    // copies need even row lengths and 16-byte aligned bases.
-    const bool vec16 = ((p | q) & 1) == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)V & 15) == 0;
+    // one 64 x 64 output block; every partial entry is written
     const size_t tsm = oz_gram_tc_smem(sym);
     auto kern = sym ? oz_gram_tc_kernel<true> : oz_gram_tc_kernel<false>;
     GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    kern<<<ns, TG_THREADS, tsm, st>>>(n, p, q, U, V, vec16 ? 1 : 0, scratch);
+    kern<<<ns, TG_THREADS, tsm, st>>>(n, p, q, U, V, vec16 ? 1 : 0, scratch, 1, 0);
+    GSI_LAUNCH_CHECK();
+  } else if (nd == ND && tp != 1) {
+    // several 64 x 64 output blocks (p or q > 64), one per blockIdx.y, each
+    // by the U != V kernel; a symmetric Gram computes the upper-triangle
+    // blocks only and is mirrored by the reduction
+    tri = sym;
+    const size_t tsm = oz_gram_tc_smem(false);
+    GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    oz_gram_tc_kernel<false><<<dim3(ns, nblk), TG_THREADS, tsm, st>>>(n, p, q, U, V, vec16 ? 1 : 0, scratch, nbj,
+                                                                     tri ? 1 : 0);
     GSI_LAUNCH_CHECK();
   } else {
     size_t smem = oz_gram_smem(nd);
@@ -1477,6 +1524,8 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
   }
   if (Gdf) {
     oz_gram_reduce_df_kernel<<<ceil_div((int64_t)p * q, 256), 256, 0, st>>>(p, q, ns, nbj, scratch, Gdf);
+  } else if (tri) {
+    oz_gram_reduce_tri_kernel<<<ceil_div(p * q, 256), 256, 0, st>>>(p, ns, nblk, nbj, scratch, G);
   } else {
     oz_gram_reduce_kernel<<<ceil_div(p * q, 256), 256, 0, st>>>(p, q, ns, nblk, sym ? 1 : 0, nbj,
                                                                 scratch, G);

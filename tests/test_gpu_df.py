@@ -158,7 +158,9 @@ def _gram_bound(U, V, rows=256):
                                        (4099, 48, 64, False), (1000, 33, 33, True), (777, 33, 17, False)])
 def test_oz_gram(G, n, p, q, sym, path):
     """Both tensor paths against the oracle's float64 Gram of the same df64
-    values (tcgen05 where p, q <= 64 on path 0; mma.sync on path 1)."""
+    values (tcgen05 on path 0 -- one 64 x 64 block, or one CTA per block
+    when p or q > 64, upper blocks only and mirrored when symmetric;
+    mma.sync on path 1)."""
     torch, gsi = G
     rng = np.random.default_rng(n * 3 + p)
     U = _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-4, 4, (1, p))))
