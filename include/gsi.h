@@ -434,9 +434,12 @@ gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, 
 /* Which tensor-core kernels the digit-split products use: 0 (default) and 2
  * the tcgen05 kernels wherever they apply (7-digit Grams of any p, q <= 128
  * and the 7-digit dense apply, one CTA per 64 x 64 output block; 7-digit
- * block products with p <= 64), 1 the mma.sync kernels everywhere (they
- * also serve the 3-digit products and block products with p > 64). Block products are identical on both
- * (same digits, exact integer digit-pair sums, same combination order).
+ * block products of any p <= 128, the contraction cut into slices of at most
+ * 64 for p > 64), 1 the mma.sync kernels everywhere (they also serve the
+ * 3-digit products). Block products with p <= 64 are identical on both
+ * (same digits, exact integer digit-pair sums, same combination order); for
+ * p > 64 the tcgen05 slices take their own digit exponents and are summed in
+ * df64, so the two agree to df64 rounding but not bit for bit.
  * Grams agree to float64-class accuracy but not bit for bit: the tcgen05
  * Gram takes its column exponents over 256-row (U == V, p <= 64) or 160-row
  * chunks,

@@ -31,8 +31,8 @@ namespace gsi {
 
 constexpr int ND = 7;
 
-// 0 and 2: tcgen05 kernels wherever they apply (block products with
-// p <= 64 per 64-column slice, Grams with p, q <= 64), 1: mma.sync kernels
+// 0 and 2: tcgen05 kernels wherever they apply (7-digit block products and
+// Grams of any p, q <= 128), 1: mma.sync kernels
 // only (set by gsi_set_tensor_path, or by GSI_TENSOR_PATH=mma / =tcgen05 at
 // the first product)
 static int g_tensor_path = -1;
@@ -129,21 +129,21 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
 }
 
 // ---------------------------------------------------------------------------
-// Right operand: B = [s_0 M_0; s_1 M_1] (K = nk*p rows, p columns, float64),
-// cut into digits with one power of two per column. Layout for the tensor
-// cores: Md[plane][n][k] (k contiguous, K16 = K rounded up to 16), F[n].
-// One block per column n.
+// Right operand: B = [s_0 M_0; s_1 M_1] restricted to the rows k0 .. k0+kw-1
+// of each M_k (K = nk*kw rows, p columns, float64), cut into digits with one
+// power of two per column. Layout for the tensor cores: Md[plane][n][k]
+// (k contiguous, K16 = K rounded up to 16), F[n]. One block per column n.
 // ---------------------------------------------------------------------------
 __global__ void oz_prep_rhs_kernel(int p, int p16, int nk, int K16, const double* M0,
                                    const double* M1, double s0, double s1,
-                                   __nv_bfloat16* Md, int* F) {
+                                   __nv_bfloat16* Md, int* F, int k0, int kw) {
   const int n = blockIdx.x;
   __shared__ float red[32];
   __shared__ int sE;
-  const int K = nk * p;
+  const int K = nk * kw;
   float mx = 0.0f;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    int kk = k / p, l = k - kk * p;
+    int kk = k / kw, l = k0 + k - kk * kw;
     double v = (n < p) ? (kk == 0 ? s0 * M0[l * p + n] : s1 * M1[l * p + n]) : 0.0;
     mx = fmaxf(mx, fabsf((float)v));
   }
@@ -161,7 +161,7 @@ __global__ void oz_prep_rhs_kernel(int p, int p16, int nk, int K16, const double
   for (int k = threadIdx.x; k < K16; k += blockDim.x) {
     double v = 0.0;
     if (k < K && n < p) {
-      int kk = k / p, l = k - kk * p;
+      int kk = k / kw, l = k0 + k - kk * kw;
       v = (kk == 0 ? s0 * M0[l * p + n] : s1 * M1[l * p + n]);
     }
     float2 x = df_from_double(v);
@@ -382,8 +382,8 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// oz_gemm on the 5th-generation tensor cores (tcgen05), for K16 <= 64 and the
-// 7-digit split. 128-row tiles; the 7 digit planes of the tile's left operand
+// oz_gemm on the 5th-generation tensor cores (tcgen05), for K16 <= 64 (one
+// slice of a longer contraction per launch) and the 7-digit split. 128-row tiles; the 7 digit planes of the tile's left operand
 // and of the right operand live in shared memory in the no-swizzle K-major
 // core-matrix layout (8 x 16-byte cores; K-adjacent cores 128 B apart, 8-row
 // groups K16/8 * 128 B apart). One thread issues the 28 digit-pair products
@@ -407,8 +407,16 @@ __device__ int g_oz_wait_limit = TC_WAIT_LIMIT;
 
 __host__ __device__ inline size_t tc_plane_bytes(int rows, int K16) { return (size_t)rows * K16 * 2; }
 
+// The left operand's digit planes; the epilogue stages the tile's combined
+// products (TC_M rows of NC + 2 float2) in the same space once the products
+// have completed, which a short contraction (K16 < 48) does not cover alone.
+__host__ __device__ inline size_t tc_a_region(int K16, int NC) {
+  const size_t planes = (size_t)ND * tc_plane_bytes(TC_M, K16), stage = (size_t)TC_M * (NC + 2) * 8;
+  return planes > stage ? planes : stage;
+}
+
 size_t oz_gemm_tc_smem(int K16, int NC) {
-  return ND * tc_plane_bytes(TC_M, K16) + ND * tc_plane_bytes(NC, K16) + (TC_M + 64) * sizeof(int) + 64;
+  return tc_a_region(K16, NC) + ND * tc_plane_bytes(NC, K16) + (TC_M + 64) * sizeof(int) + 64;
 }
 
 __device__ __forceinline__ uint32_t tc_off(int r, int k, int K16) {
@@ -471,7 +479,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   const int NC = min(64, p16 - col0);
   const uint32_t aplane = (uint32_t)tc_plane_bytes(TC_M, K16), bplane = (uint32_t)tc_plane_bytes(NC, K16);
   unsigned char* Ad = smem;
-  unsigned char* Bd = Ad + ND * aplane;
+  unsigned char* Bd = Ad + tc_a_region(K16, NC);
   int* Er = reinterpret_cast<int*>(Bd + ND * bplane);
   int* Fs = Er + TC_M;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Fs + 64);  // [0] products, [1] drain
@@ -524,9 +532,9 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     for (int c = 0; c < 8; ++c) {
       const int k = 8 * c + 2 * j;
       float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
-      if (live && k < p) {
-        const int64_t o = R * p + k;
-        if (a.vec16 && k + 1 < p && (o & 1) == 0) {  // 16-byte aligned pair
+      if (live && k < a.kw) {
+        const int64_t o = R * a.ldu + a.kofs + k;
+        if (a.vec16 && k + 1 < a.kw && (o & 1) == 0) {  // 16-byte aligned pair
           const float4 v = *reinterpret_cast<const float4*>(a.U[0] + o);
           x0 = make_float2(v.x, v.y);
           x1 = make_float2(v.z, v.w);
@@ -538,7 +546,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
         } else {
           x0 = a.U[0][o];
           if (two) x0 = df_add(x0, df_mul(a.a1, a.U[1][o]));
-          if (k + 1 < p) {
+          if (k + 1 < a.kw) {
             x1 = a.U[0][o + 1];
             if (two) x1 = df_add(x1, df_mul(a.a1, a.U[1][o + 1]));
           }
@@ -635,10 +643,10 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // (c) epilogue, part 1: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its
     // rows) and the column quarter w / 4, 4 columns at a time; the combined
-    // and scaled products go to shared memory (the digit planes are free once
-    // the products completed: 128 (NC + 2) float2 <= 7 * 128 * K16 bf16 for
-    // NC <= K16, K16 >= 16), row stride NC + 2 float2 so that every row starts
-    // on 16 bytes (16-byte stores and loads, four wavefronts per warp access)
+    // and scaled products go to shared memory (the left digit planes' space,
+    // free once the products completed and sized for both), row stride
+    // NC + 2 float2 so that every row starts on 16 bytes (16-byte stores and
+    // loads, four wavefronts per warp access)
     float2* stage = reinterpret_cast<float2*>(Ad);
     const int ss = NC + 2;
     if (!issuer) {
@@ -956,8 +964,8 @@ oz_gram_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const floa
 }
 
 // ---------------------------------------------------------------------------
-// oz_gram on the 5th-generation tensor cores, for p, q <= 64 and the 7-digit
-// split. Rows go in exponent chunks of EC rows (256 for U == V, 160
+// oz_gram on the 5th-generation tensor cores, one 64 x 64 output block per
+// blockIdx.y (p, q <= 128), and the 7-digit split. Rows go in exponent chunks of EC rows (256 for U == V, 160
 // otherwise), staged raw in shared memory by cp.async; the column exponents
 // are taken over the whole chunk, and the chunk's digit-pair products are
 // summed in tensor memory over its sub-chunks of SK rows (32, resp. 16) before
@@ -1382,8 +1390,6 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   __nv_bfloat16* Md = reinterpret_cast<__nv_bfloat16*>(rhs_ws);
   int* F = reinterpret_cast<int*>(reinterpret_cast<char*>(rhs_ws) +
                                   (size_t)ND * p16 * K16 * sizeof(__nv_bfloat16));
-  oz_prep_rhs_kernel<<<p16, 128, 0, st>>>(p, p16, 1, K16, M[0], M[0], s[0], 0.0, Md, F);
-  GSI_LAUNCH_CHECK();
   OzGemmArgs a{};
   a.U[0] = U[0];
   a.U[1] = fuse ? U[1] : U[0];
@@ -1400,6 +1406,9 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   a.dot_part = dot_part;
   a.dot_with = dot_with;
   a.dot_self = dot_self ? 1 : 0;
+  a.ldu = p;
+  a.kofs = 0;
+  a.kw = p;
   {
     const void* ptrs[6] = {a.U[0], a.U[1], ne > 0 ? E[0] : nullptr, ne > 1 ? E[1] : nullptr, dot_with, out};
     a.vec16 = 1;
@@ -1407,21 +1416,52 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
       if (((uintptr_t)q & 15) != 0) a.vec16 = 0;
   }
   const int NCmax = std::min(64, p16);
-  if (nd == ND && K16 <= 64 && tensor_path() != 1) {
-    const size_t tsm = oz_gemm_tc_smem(K16, NCmax);
-    GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+  if (nd == ND && tensor_path() != 1) {
+    // The tcgen05 kernel holds a 128-row tile of the left operand's digits for
+    // a contraction of at most 64: a longer one (p > 64) is cut into nks
+    // slices of equal width kc, one launch each. Every slice is an exact
+    // digit product with its own row and column powers of two; the slices
+    // are summed in df64 through the output (E_0 = OUT, c_0 = 1 from the
+    // second slice on), the caller's elementwise terms go with the first
+    // slice and the dot partials are taken on the last, which writes OUT.
+    const int nks = (p16 + 63) / 64;
+    const int kc = std::min(p, pad16((p + nks - 1) / nks));
     int gx = (int)std::min<int64_t>((n + TC_M - 1) / TC_M, (int64_t)sm_count());
     gx = std::max(gx, 1);
     if (nparts) *nparts = gx * ncs;
     // the row sums are formed where one warp holds whole rows (the kernel's
     // row-wise epilogue: one column block, even p, aligned blocks)
     const bool rows = rinf_part && a.vec16 && ncs == 1 && (p & 1) == 0;
-    a.rinf_part = rows ? rinf_part : nullptr;
     if (rinf_done) *rinf_done = rows;
-    oz_gemm_tc_kernel<<<dim3(gx, ncs), TC_THREADS, tsm, st>>>(n, p, p16, K16, a);
-    GSI_LAUNCH_CHECK();
+    for (int h = 0; h < nks; ++h) {
+      const int k0 = h * kc, kw = std::min(kc, p - k0);
+      const int K16h = pad16(kw);
+      oz_prep_rhs_kernel<<<p16, 128, 0, st>>>(p, p16, 1, K16h, M[0], M[0], s[0], 0.0, Md, F, k0, kw);
+      GSI_LAUNCH_CHECK();
+      OzGemmArgs b = a;
+      b.kofs = k0;
+      b.kw = kw;
+      if (h > 0) {
+        b.ne = 1;
+        b.E[0] = out;
+        b.ce[0] = make_float2(1.f, 0.f);
+      }
+      const bool last = h == nks - 1;
+      if (!last) {
+        b.dot_part = nullptr;
+        b.dot_with = nullptr;
+        b.dot_self = 0;
+      }
+      b.rinf_part = last && rows ? rinf_part : nullptr;
+      const size_t tsm = oz_gemm_tc_smem(K16h, NCmax);
+      GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+      oz_gemm_tc_kernel<<<dim3(gx, ncs), TC_THREADS, tsm, st>>>(n, p, p16, K16h, b);
+      GSI_LAUNCH_CHECK();
+    }
     return GSI_OK;
   }
+  oz_prep_rhs_kernel<<<p16, 128, 0, st>>>(p, p16, 1, K16, M[0], M[0], s[0], 0.0, Md, F, 0, p);
+  GSI_LAUNCH_CHECK();
   size_t smem = oz_gemm_smem(K16, NCmax, fuse ? 2 : 1, nd);
   auto kern = nd == 3 ? oz_gemm_kernel<3> : oz_gemm_kernel<ND>;
   GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -22,6 +22,8 @@ struct OzGemmArgs {
   int dot_self;
   int vec16;                 // every block pointer 16-byte aligned: 16-byte loads and stores
   float* rinf_part;          // per-block max_r sum_j |hi(out[r,j])| (row-wise epilogue only) or null
+  int ldu, kofs, kw;         // tcgen05 kernel: the left operand is columns kofs .. kofs+kw-1 of
+                             // the row-major n x ldu blocks U (a slice of the contraction)
 };
 
 int pad16(int x);

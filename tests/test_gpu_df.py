@@ -274,6 +274,45 @@ def test_oz_gemm_tcgen05_equals_mma(G, n, p, fused, ne):
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("n,p,fused,ne", [(4099, 128, True, 2), (3001, 72, False, 1), (1000, 65, True, 0),
+                                          (20011, 100, False, 2), (257, 128, False, 0)])
+def test_oz_gemm_tcgen05_contraction_slices(G, n, p, fused, ne):
+    """p > 64: the tcgen05 block product cuts the contraction into slices of
+    at most 64 (each an exact digit product with its own exponents) and sums
+    them in df64, so it is a different rounding of the same product than the
+    mma.sync kernel's single pass: both within the digit-split bound of the
+    float64 product of the exact df64 inputs, and within twice that of each
+    other. Odd p puts every other row's start 8 bytes off a 16-byte boundary."""
+    torch, gsi = G
+    rng = np.random.default_rng(n + 5 * p)
+    U0h = _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-3, 3, (n, 1))))
+    U1h = _exact(gsi, rng.standard_normal((n, p))) if fused else None
+    Mh = rng.standard_normal((p, p)) * np.exp(rng.uniform(-2, 2, (1, p)))
+    Eh = [_exact(gsi, rng.standard_normal((n, p))) for _ in range(ne)]
+    c = [0.3, -2.5][:ne]
+    s0, s1 = 0.7, 0.3
+    U0, M = _df_dev(torch, gsi, U0h), torch.from_numpy(Mh).cuda()
+    U1 = _df_dev(torch, gsi, U1h) if fused else None
+    E = [_df_dev(torch, gsi, e) for e in Eh]
+    outs = []
+    for path in (2, 1):
+        gsi.set_tensor_path(path)
+        out = torch.zeros((n, p, 2), dtype=torch.float32, device="cuda")
+        gsi.oz_gemm(U0, M, out, s0=s0, U1=U1, M1=M if fused else None, s1=s1 if fused else 0.0, E=E, c=c)
+        outs.append(gsi.from_df(out.cpu().numpy()))
+    gsi.set_tensor_path(0)
+    # the fused left operand s0 (U0 + (s1/s0) U1) is formed in df64 first
+    L = s0 * U0h + (s1 * U1h if fused else 0.0)
+    ref = L @ Mh + sum(cm * Em for cm, Em in zip(c, Eh))
+    bound = (s0 * np.abs(U0h) + (s1 * np.abs(U1h) if fused else 0.0)).max(1, keepdims=True) \
+        * np.abs(Mh).max(0, keepdims=True) * p * 2.0 ** -44
+    bound = bound + sum(abs(cm) * np.abs(Em) for cm, Em in zip(c, Eh)) * 2.0 ** -46 + np.abs(ref) * 2.0 ** -46
+    for o in outs:
+        assert np.all(np.abs(o - ref) <= bound)
+    assert np.all(np.abs(outs[0] - outs[1]) <= 2 * bound)
+    assert np.linalg.norm(outs[0] - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("n,p,q,sym", [(100003, 64, 64, True), (100003, 64, 64, False), (4097, 17, 40, False),
                                        (70, 8, 8, True), (200000, 48, 5, False)])
 def test_oz_gram_tcgen05_and_mma_agree(G, n, p, q, sym):
