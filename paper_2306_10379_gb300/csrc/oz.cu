@@ -1006,7 +1006,7 @@ struct TgGeom {
   static constexpr uint32_t DBUF = SYM ? 32768u : 28672u;
   static constexpr size_t smem() {
     return (size_t)RAWR * TG_RS * sizeof(float2) + 2 * DBUF + NG * 64 * sizeof(float) + 128 * sizeof(int) +
-           64;
+           128 * sizeof(float) + 64;
   }
 };
 static_assert(TgGeom<true>::smem() <= 227 * 1024 && TgGeom<false>::smem() <= 227 * 1024, "shared memory");
@@ -1014,6 +1014,43 @@ static_assert(TgGeom<false>::EC % (2 * TgGeom<false>::SK) == 0 && TgGeom<true>::
               "an even number of sub-chunks per chunk");
 
 size_t oz_gram_tc_smem(bool sym) { return sym ? TgGeom<true>::smem() : TgGeom<false>::smem(); }
+
+// digitsN with the frame's scale s = 2^(7-E) given; the rounding constants
+// 1.5 * 2^(23 - 7i) as literals
+template <int N>
+__device__ __forceinline__ void digits_scaled(float h, float l, float s, float d[N]) {
+  constexpr float kRound[7] = {12582912.0f, 98304.0f, 768.0f, 6.0f, 0.046875f, 0.0003662109375f,
+                               2.86102294921875e-06f};
+  float a = __fmul_rn(h, s);
+  const float b = __fmul_rn(l, s);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (i == 3) a = __fadd_rn(a, b);
+    const float di = __fsub_rn(__fadd_rn(a, kRound[i]), kRound[i]);
+    d[i] = di;
+    if (i + 1 < N) a = __fsub_rn(a, di);
+  }
+}
+
+// sum_g S_g as df64 (S_g an exact integer times 2^(-7 (g + g0)), g0 = 0 or
+// 1, from a 64 x 64 block's chunk): the groups of weight 2^-28 and below are
+// added in float32 (their rounding stays below 2^-52 of the chunk's scale,
+// far under the 2^-49 of the digit cut), the others by TwoSum from the
+// smallest up
+template <int N, int NEXACT>
+__device__ __forceinline__ float2 combine_groups_fast(const float S[N]) {
+  float h = S[N - 1];
+#pragma unroll
+  for (int g = N - 2; g >= NEXACT; --g) h = __fadd_rn(S[g], h);
+  float l = 0.0f;
+#pragma unroll
+  for (int g = NEXACT - 1; g >= 0; --g) {
+    const float2 t = two_sum(S[g], h);
+    h = t.x;
+    l = __fadd_rn(l, t.y);
+  }
+  return fast_two_sum(h, l);
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -1052,7 +1089,9 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   float* cmx = reinterpret_cast<float*>(dig + 2 * TG_DBUF);  // [NG][64] partial column maxima
   int* Eu = reinterpret_cast<int*>(cmx + NG * 64);  // after all NG groups of maxima
   int* Ev = Eu + 64;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Ev + 64);     // one per digit buffer, then the drain
+  float* Fu = reinterpret_cast<float*>(Ev + 64);  // the exponents as scales 2^(E-7)
+  float* Fv = Fu + 64;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Fv + 64);     // one per digit buffer, then the drain
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool issuer = warp == TG_WORKERS / 32;
@@ -1084,7 +1123,7 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   const uint32_t dbase = smem_addr(dig);
   const uint32_t mb0 = smem_addr(mbar), mb1 = smem_addr(mbar + 1);
   uint32_t ph0 = 0u, ph1 = 0u;  // phases of the two buffers' barriers
-  const int* Evv = SYM ? Eu : Ev;
+  const float* Fvv = SYM ? Fu : Fv;
   // combine: worker warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. output
   // row a = 32 (w % 2) + lane of the top (w % 4 < 2) or bottom half, columns
   // 16 (w / 4) .. + 15
@@ -1124,6 +1163,38 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
     cp_async_commit();
   };
 
+  // the rows of sub-chunk sub only (SK rows of U, and of V), into the raw
+  // rows that sub-chunk occupies: restaged for the next chunk as soon as the
+  // current chunk's sub-chunk has been cut, so that the copies spread over
+  // the chunk instead of queueing at its end
+  auto stage_sub = [&](int64_t ch, int sub) {
+    const int64_t r0 = ch * EC + sub * SK;
+    if (vec16) {
+      for (int e = tid; e < 2 * SK * 32 / (SYM ? 2 : 1); e += TG_WORKERS) {
+        const int rr = e >> 5, c = 2 * (e & 31);
+        const bool isv = !SYM && rr >= SK;
+        const int lr = isv ? rr - SK : rr;
+        const int64_t R = r0 + lr;
+        const int ld = isv ? q : p;
+        const float2* src = (isv ? V + cv0 : U + cu0);
+        const bool ok = R < n && c < (isv ? wv : wu);
+        cp_async16(raw + ((isv ? EC : 0) + sub * SK + lr) * TG_RS + c, src + (ok ? R * ld + c : 0), ok);
+      }
+    } else {
+      for (int e = tid; e < 2 * SK * 64 / (SYM ? 2 : 1); e += TG_WORKERS) {
+        const int rr = e >> 6, c = e & 63;
+        const bool isv = !SYM && rr >= SK;
+        const int lr = isv ? rr - SK : rr;
+        const int64_t R = r0 + lr;
+        const int ld = isv ? q : p;
+        const float2* src = (isv ? V + cv0 : U + cu0);
+        const bool ok = R < n && c < (isv ? wv : wu);
+        cp_async8(raw + ((isv ? EC : 0) + sub * SK + lr) * TG_RS + c, src + (ok ? R * ld + c : 0), ok);
+      }
+    }
+    cp_async_commit();
+  };
+
   // digit item of this worker (one per sub-chunk): column c, rows
   // 4 qd .. 4 qd + 3 of the sub-chunk, of U or (isv) of V. Lanes cover 8
   // columns x 2 quads x 2 row octets, so a warp's 8-byte stores fill 2 x 32
@@ -1154,8 +1225,14 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
       const int c = tid & 63, g0 = (tid < 64) ? 0 : NG / 2, ng = SYM ? NG : NG / 2;
       float m = 0.f;
       for (int g = g0; g < g0 + ng; ++g) m = fmaxf(m, cmx[g * 64 + c]);
-      if (tid < 64) Eu[c] = exponent_above(m);
-      else Ev[c] = exponent_above(m);
+      const int E = exponent_above(m);
+      if (tid < 64) {
+        Eu[c] = E;
+        Fu[c] = exp2i(E - 7);
+      } else {
+        Ev[c] = E;
+        Fv[c] = exp2i(E - 7);
+      }
     }
     __syncthreads();
     // (b) sub-chunks: cut into digit buffer s % 2, products on the tensor core
@@ -1169,12 +1246,12 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
       if (!issuer && ok) {
         unsigned char* dst = dig + buf * TG_DBUF + (isv ? 7 * plane : 0);
         const int r = irow + s * SK;
-        const int E = (isv ? Ev : Eu)[ic];
+        const float scut = exp2i(7 - (isv ? Ev : Eu)[ic]);
         float d[4][ND];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const float2 x = raw[(r + t) * TG_RS + ic];
-          digitsN<ND>(x.x, x.y, E, d[t]);
+          digits_scaled<ND>(x.x, x.y, scut, d[t]);
         }
 #pragma unroll
         for (int i = 0; i < ND; ++i)
@@ -1219,8 +1296,8 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
                        : "memory");
         }
         __syncwarp();
-      } else if (s == NSUB - 1 && ch + gridDim.x < nchunks) {
-        stage(ch + gridDim.x);  // raw rows are free
+      } else if (ch + gridDim.x < nchunks) {
+        stage_sub(ch + gridDim.x, s);  // sub-chunk s's raw rows are free (every worker cut it)
       }
     }
     if (failed) break;
@@ -1238,6 +1315,7 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
     ph1 ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!issuer) {
+      const float fu = Fu[arow];
       const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll
       for (int c0 = 0; c0 < 16; c0 += 4) {
@@ -1253,10 +1331,10 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
           for (int h = 0; h < ND; ++h) S[h] = __uint_as_float(v[h][e]);
           // top: groups 0..6 (even digits of U); bottom: groups 1..6 (odd
           // digits), block h holding group h + 1, each sum carrying its weight
-          const float2 w = top ? combine_groups<ND>(S) : combine_groups<ND - 1>(S);
-          const int sc = Eu[arow] + Evv[cb + c0 + e] - 14;
-          const float f1 = exp2i(sc / 2), f2 = exp2i(sc - sc / 2);
-          res[c0 + e] = df_add(res[c0 + e], make_float2(w.x * f1 * f2, w.y * f1 * f2));
+          // groups 4..6 in float32
+          const float2 w = top ? combine_groups_fast<ND, 4>(S) : combine_groups_fast<ND - 1, 3>(S);
+          const float fv = Fvv[cb + c0 + e];
+          res[c0 + e] = df_add(res[c0 + e], make_float2(w.x * fu * fv, w.y * fu * fv));
         }
       }
     }
