@@ -96,6 +96,27 @@ __device__ __forceinline__ float2 combine_groups(const float S[N]) {
   return fast_two_sum(h, l);
 }
 
+// sum_g S_g as df64 like combine_groups, with the groups NEXACT .. N - 1 (of
+// weight 2^-28 and below when NEXACT = 4 and g0 = 0) added in float32: their
+// rounding stays below 2^-52 of the product's scale, far under the 2^-49 of
+// the digit cut; the others by TwoSum from the smallest up. S_g is an exact
+// integer times 2^(-7 (g + g0)), g0 = 0 or 1. NEXACT = N - 1 is combine_groups.
+template <int N, int NEXACT>
+__device__ __forceinline__ float2 combine_groups_fast(const float S[N]) {
+  static_assert(NEXACT >= 1 && NEXACT < N, "S[N - 1] starts the sum");
+  float h = S[N - 1];
+#pragma unroll
+  for (int g = N - 2; g >= NEXACT; --g) h = __fadd_rn(S[g], h);
+  float l = 0.0f;
+#pragma unroll
+  for (int g = NEXACT - 1; g >= 0; --g) {
+    const float2 t = two_sum(S[g], h);
+    h = t.x;
+    l = __fadd_rn(l, t.y);
+  }
+  return fast_two_sum(h, l);
+}
+
 __device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
   uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -328,7 +349,8 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
           float S[NDT];
 #pragma unroll
           for (int g = 0; g < NDT; ++g) S[g] = acc[g][t][h * 2 + e2];
-          float2 w = combine_groups<NDT>(S);
+          // the same combination as the tcgen05 block product (bit-identical results)
+          float2 w = combine_groups_fast<NDT, (NDT > 4 ? 4 : NDT - 1)>(S);
           int sc = Er[rr] + Fs[cc + e2] - 14;
           if (sc >= -126) {
             float f = exp2i(sc);
@@ -664,7 +686,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
           float S[ND];
 #pragma unroll
           for (int g = 0; g < ND; ++g) S[g] = __uint_as_float(v[g][e2]);
-          const float2 w = combine_groups<ND>(S);
+          const float2 w = combine_groups_fast<ND, 4>(S);
           const int sc = Er[row] + Fs[c0 + e2] - 14;
           if (sc >= -126) {
             const float f = exp2i(sc);
@@ -1032,25 +1054,6 @@ __device__ __forceinline__ void digits_scaled(float h, float l, float s, float d
   }
 }
 
-// sum_g S_g as df64 (S_g an exact integer times 2^(-7 (g + g0)), g0 = 0 or
-// 1, from a 64 x 64 block's chunk): the groups of weight 2^-28 and below are
-// added in float32 (their rounding stays below 2^-52 of the chunk's scale,
-// far under the 2^-49 of the digit cut), the others by TwoSum from the
-// smallest up
-template <int N, int NEXACT>
-__device__ __forceinline__ float2 combine_groups_fast(const float S[N]) {
-  float h = S[N - 1];
-#pragma unroll
-  for (int g = N - 2; g >= NEXACT; --g) h = __fadd_rn(S[g], h);
-  float l = 0.0f;
-#pragma unroll
-  for (int g = NEXACT - 1; g >= 0; --g) {
-    const float2 t = two_sum(S[g], h);
-    h = t.x;
-    l = __fadd_rn(l, t.y);
-  }
-  return fast_two_sum(h, l);
-}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
