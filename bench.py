@@ -44,8 +44,8 @@ GPU_ITERS_TO_TOL = {("cg", 128, 64): 4953}
 # elementwise terms; the CSR SpMM). None where a kernel changed after its
 # capture.
 NCU_TRAFFIC = {
-    "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.319e6 + 3.630e6) + 3 * (524.560e6 + 3.676e6)) / 5},
-    "blockmul": {"n": 512000, "p": 64, "bytes": (2 * (524.473e6 + 224.485e6) + 2 * (786.623e6 + 238.002e6)) / 4},
+    "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.231e6 + 3.466e6) + 3 * (524.441e6 + 3.660e6)) / 5},
+    "blockmul": {"n": 512000, "p": 64, "bytes": (2 * (524.494e6 + 224.528e6) + 2 * (786.619e6 + 238.081e6)) / 4},
     "spmm": {"n": 512000, "p": 64, "bytes": 308.8e6 + 229.4e6},
 }
 TRAFFIC_SOURCE = "one-kernel ncu captures at 80^3 (n = 512,000, p = 64), scaled by rows"
