@@ -1375,6 +1375,518 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
   }
 }
 
+// ---------------------------------------------------------------------------
+// oz_gram_tc_ring_kernel: the tcgen05 Gram for 16-byte aligned blocks of even
+// width (one 64 x 64 output block per blockIdx.y, as oz_gram_tc_kernel).
+//
+// The kernel above stages a whole exponent chunk raw, which fills shared
+// memory and leaves room for two digit buffers only; its sub-chunk loop then
+// waits on the tensor core every other sub-chunk, and the chunk stays short.
+// Here the column exponents of a chunk come from a separate maxima warp that
+// reads the chunk's rows one chunk ahead of the workers: 1D bulk copies
+// (cp.async.bulk, completion counted on an mbarrier per slot, no registers
+// held) of whole rows into a small ring of slots, reduced from shared memory.
+// The workers then stage the rows raw sub-chunk by sub-chunk through a ring
+// of NR slots (16-byte cp.async, NR - 1 sub-chunks ahead; the rows come from
+// L2, where the maxima warp's read left them), cut them into NB digit
+// buffers with one mbarrier each, and combine once per chunk of EC rows
+// (512 for U == V, 256 otherwise; 256-row chunks keep U != V's two reads of
+// a row within L2 reach). Exactness of the accumulators: as for
+// oz_gram_tc_kernel, 28800 EC < 2^24 for chunks of up to 582 rows.
+//
+// Roles: warps 0..15 stage, cut and combine; warp 16 issues the products;
+// warps 17 and 18 compute the maxima, each reducing half of every slot
+// (reading a chunk's rows costs one warp more issue slots than it gets
+// beside four busy workers), warp 17 also issuing the copies. Workers and the
+// issuing warp meet at named barrier 1 every sub-chunk, the maxima warps at
+// named barrier 2 every slot; all 19 warps meet at barrier 0 once per chunk,
+// where the maxima warps hand over the next chunk's exponents. Every thread
+// passes the same sequence of barrier-0 arrivals whatever fails: a timeout
+// only turns later work off (and the partial sums into NaN).
+// ---------------------------------------------------------------------------
+constexpr int TR_WORKERS = 512;
+constexpr int TR_THREADS = TR_WORKERS + 96;  // + the issuing warp + two maxima warps
+constexpr int TR_BAR_COUNT = TR_WORKERS + 32;
+template <bool SYM>
+struct TrGeom {
+  static constexpr int EC = SYM ? 512 : 256;       // exponent chunk rows
+  static constexpr int SK = SYM ? 32 : 16;         // sub-chunk rows
+  static constexpr int NSUB = EC / SK;             // sub-chunks per chunk
+  static constexpr int NB = 3;                     // digit buffers
+  static constexpr int NR = 4;                     // raw slots (staging NR - 1 sub-chunks ahead)
+  static constexpr int MSW = SYM ? 3 : 4;          // maxima slots per maxima warp
+  static constexpr int MS = 2 * MSW;
+  static constexpr int MB = SYM ? 16 : 8;          // rows per operand in one maxima slot
+  static constexpr int NMB = EC / MB;              // maxima batches per chunk
+  static constexpr uint32_t PLANE = 64u * SK * 2;  // one digit plane: 64 columns x SK rows, bf16
+  static constexpr uint32_t DBUF = (SYM ? 8u : 14u) * PLANE;
+  static constexpr size_t RAW_SLOT = (size_t)32 * TG_RS * sizeof(float2);
+  static constexpr size_t MSLOT = (size_t)16 * 64 * sizeof(float2);  // 16 rows of 64 df64
+  // raw slots, digit buffers, maxima slots, exponents and scales [2][128]
+  // each, the maxima warps' scratch [128], two flags, barriers (digit
+  // buffers, drain, maxima slots), TMEM slot
+  static constexpr size_t smem() {
+    return NR * RAW_SLOT + NB * (size_t)DBUF + MS * MSLOT + 2 * 256 * sizeof(int) + 128 * sizeof(float) + 16 +
+           (NB + 1 + MS) * sizeof(uint64_t) + 16;
+  }
+};
+static_assert(TrGeom<true>::smem() <= 227 * 1024 && TrGeom<false>::smem() <= 227 * 1024, "shared memory");
+static_assert(TrGeom<true>::NR == 4 && TrGeom<false>::NR == 4, "wait_group<NR - 2> below");
+static_assert(TrGeom<false>::NR * TrGeom<false>::RAW_SLOT >= 64 * 65 * sizeof(float2) &&
+                  TrGeom<true>::NR * TrGeom<true>::RAW_SLOT >= 64 * 65 * sizeof(float2),
+              "final stage fits the raw ring");
+
+size_t oz_gram_tc_ring_smem(bool sym) { return sym ? TrGeom<true>::smem() : TrGeom<false>::smem(); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// named barrier 2 (the two maxima warps) with an OR over v
+__device__ __forceinline__ bool bar2_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 2, 64, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+// named barrier 1 (workers and the issuing warp) with an OR over v
+__device__ __forceinline__ bool bar1_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(TR_BAR_COUNT)
+      : "memory");
+  return r != 0;
+}
+
+template <bool SYM>
+__global__ void __launch_bounds__(TR_THREADS, 1)
+oz_gram_tc_ring_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
+                       float2* part, int nbj, int tri) {
+  using Geo = TrGeom<SYM>;
+  int bi = 0, bj = (int)blockIdx.y;
+  if (tri) {
+    int y = (int)blockIdx.y;
+    while (y >= nbj - bi) {
+      y -= nbj - bi;
+      ++bi;
+    }
+    bj = bi + y;
+  } else {
+    bi = (int)blockIdx.y / nbj;
+    bj = (int)blockIdx.y - bi * nbj;
+  }
+  const int cu0 = 64 * bi, cv0 = 64 * bj;
+  const int wu = min(64, p - cu0), wv = min(64, q - cv0);  // live columns (even: p, q even)
+  constexpr int EC = Geo::EC, SK = Geo::SK, NSUB = Geo::NSUB, NB = Geo::NB, NR = Geo::NR;
+  constexpr int MS = Geo::MS, MSW = Geo::MSW, MB = Geo::MB, NMB = Geo::NMB;
+  static_assert(NMB % 2 == 0, "the maxima warps take alternate batches");
+  constexpr uint32_t plane = Geo::PLANE, DBUF = Geo::DBUF;
+  extern __shared__ __align__(16) unsigned char tr_smem[];
+  float2* raw = reinterpret_cast<float2*>(tr_smem);  // NR slots of 32 rows
+  unsigned char* dig = tr_smem + NR * Geo::RAW_SLOT;
+  float2* mslot = reinterpret_cast<float2*>(dig + NB * DBUF);  // MS slots of 16 rows x 64
+  int* Ex = reinterpret_cast<int*>(mslot + MS * 16 * 64);     // [chunk parity][U's 64, V's 64]
+  float* Fx = reinterpret_cast<float*>(Ex + 256);              // the same as scales 2^(E-7)
+  volatile float* mscr = Fx + 256;                              // maxima warp 1's maxima, [U's 64, V's 64]
+  volatile int* flags = reinterpret_cast<volatile int*>(Fx + 384);  // [0] workers failed, [1] maxima failed
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Fx + 384 + 4);  // NB digit buffers, drain, MS maxima slots
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + NB + 1 + MS);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool issuer = warp == TR_WORKERS / 32, maxw = warp > TR_WORKERS / 32;
+  const int mw = warp - TR_WORKERS / 32 - 1;  // maxima warp 0 or 1
+  const bool worker = tid < TR_WORKERS;
+  if (SYM && worker)
+    for (int e = tid; e < NB * (int)(plane / 16); e += TR_WORKERS) {
+      const int b = e / (int)(plane / 16), o = e - b * (int)(plane / 16);
+      *reinterpret_cast<uint4*>(dig + b * DBUF + 7 * plane + 16 * o) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < NB + 1 + MS; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + b)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    flags[0] = 0;
+    flags[1] = 0;
+  }
+  const int nchunks = (int)((n + EC - 1) / EC);  // n < 2^34 (checked by the caller)
+  const int nmy = (int)blockIdx.x < nchunks ? (nchunks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int G = nmy * NSUB;
+  const uint32_t mbase = smem_addr(mbar), msbase = smem_addr(mbar + NB + 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int wait_limit = g_oz_wait_limit;
+
+  if (maxw) {
+    // ---- the maxima warps: chunk j's column maxima, one chunk ahead ----
+    // batch gb = j NMB + b covers rows b MB .. b MB + MB - 1 of this CTA's
+    // chunk j: cells 0..MB-1 hold U's rows, cells MB..15 V's (U != V). The
+    // warps take alternate batches (b % 2 == mw; NMB is even), each through
+    // its own ring of MSW slots, and merge their maxima once per chunk.
+    // Where the block spans whole rows (64 columns or fewer), a batch's rows
+    // are contiguous: one copy per operand, rows ld apart in the slot;
+    // otherwise one copy per row, rows 64 apart (the copy engine's cost per
+    // copy made 16 copies of 512 B per batch the bottleneck).
+    const int total = nmy * NMB / 2;  // this warp's batches
+    const bool contU = wu == p, contV = SYM ? contU : wv == q;
+    const int strU = contU ? p : 64, strV = contV ? q : 64;
+    auto batch_rows = [&](int t, int64_t& R0) {  // first row of this warp's t-th batch
+      const int gb = 2 * t + mw;
+      const int j = gb / NMB, b = gb - j * NMB;
+      R0 = ((int64_t)blockIdx.x + (int64_t)j * gridDim.x) * EC + (int64_t)b * MB;
+    };
+    auto slot_of = [&](int t) { return mslot + (size_t)(mw * MSW + t % MSW) * 16 * 64; };
+    auto bar_of = [&](int t) { return msbase + 8u * (uint32_t)(mw * MSW + t % MSW); };
+    auto issue = [&](int t) {
+      int64_t R0;
+      batch_rows(t, R0);
+      const int64_t left = n - R0;
+      const int nv = left <= 0 ? 0 : (left < MB ? (int)left : MB);
+      float2* sl = slot_of(t);
+      uint32_t bytes = 0;
+      const float2* src = U;
+      float2* dst = sl;
+      if (contU) {
+        if (lane == 0 && nv > 0) {
+          bytes = (uint32_t)nv * (uint32_t)p * 8u;
+          src = U + (size_t)R0 * p;
+        }
+      } else if (lane < MB && lane < nv) {
+        bytes = (uint32_t)wu * 8u;
+        src = U + (size_t)(R0 + lane) * p + cu0;
+        dst = sl + lane * 64;
+      }
+      if (!SYM) {
+        if (contV) {
+          if (lane == 16 && nv > 0) {
+            bytes = (uint32_t)nv * (uint32_t)q * 8u;
+            src = V + (size_t)R0 * q;
+            dst = sl + MB * 64;
+          }
+        } else if (lane >= 16 && lane < 16 + MB && lane - 16 < nv) {
+          bytes = (uint32_t)wv * 8u;
+          src = V + (size_t)(R0 + lane - 16) * q + cv0;
+          dst = sl + (MB + lane - 16) * 64;
+        }
+      }
+      const uint32_t tot = __reduce_add_sync(0xffffffffu, bytes);
+      const uint32_t mb = bar_of(t);
+      if (lane == 0)
+        asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(mb),
+                     "r"(tot)
+                     : "memory");
+      __syncwarp();
+      if (bytes)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_addr(dst)),
+            "l"(src), "r"(bytes), "r"(mb)
+            : "memory");
+    };
+    const bool lu = 2 * lane < wu, lv = 2 * lane < wv;
+    float mu0 = 0.f, mu1 = 0.f, mv0 = 0.f, mv1 = 0.f;  // columns 2 lane, 2 lane + 1 of U and V
+    bool dead = false;
+    int issued_t = 0, done_t = 0;
+    for (; issued_t < MSW - 1 && issued_t < total; ++issued_t) issue(issued_t);
+    for (int j = 0; j <= nmy; ++j) {
+      if (j < nmy) {
+        for (int t = j * (NMB / 2); t < (j + 1) * (NMB / 2); ++t) {
+          if (dead) break;
+          if (issued_t < total) issue(issued_t++);
+          if (!tc_wait(bar_of(t), (uint32_t)((t / MSW) & 1), wait_limit)) {
+            dead = true;
+            if (lane == 0) {
+              atomicAdd(&g_oz_tc_timeouts, 1);
+              flags[1] = 1;
+            }
+            break;
+          }
+          done_t = t + 1;
+          int64_t R0;
+          batch_rows(t, R0);
+          const int64_t left = n - R0;  // cells i % MB below it are live
+          const float2* sl = slot_of(t) + 2 * lane;
+          if (left >= MB && lu && (SYM || lv)) {
+            float4 v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const bool isvc = !SYM && i >= MB;
+              v[i] = *reinterpret_cast<const float4*>(sl + (isvc ? MB * 64 + (i - MB) * strV : i * strU));
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              if (!SYM && i >= MB) {
+                mv0 = fmaxf(mv0, fabsf(v[i].x));
+                mv1 = fmaxf(mv1, fabsf(v[i].z));
+              } else {
+                mu0 = fmaxf(mu0, fabsf(v[i].x));
+                mu1 = fmaxf(mu1, fabsf(v[i].z));
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const bool isvc = !SYM && i >= MB;
+              const int li = isvc ? i - MB : i;
+              if (li < left && (isvc ? lv : lu)) {
+                const float4 v =
+                    *reinterpret_cast<const float4*>(sl + (isvc ? MB * 64 + li * strV : li * strU));
+                if (isvc) {
+                  mv0 = fmaxf(mv0, fabsf(v.x));
+                  mv1 = fmaxf(mv1, fabsf(v.z));
+                } else {
+                  mu0 = fmaxf(mu0, fabsf(v.x));
+                  mu1 = fmaxf(mu1, fabsf(v.z));
+                }
+              }
+            }
+          }
+          // the slot's generic reads before the next bulk copy into it
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+        }
+        // chunk j's exponents and scales (parity slot j & 1; the workers
+        // finished chunk j - 2, its last user, before the last barrier):
+        // warp 1's maxima through the scratch, then warp 0 publishes
+        const int es = j & 1;
+        if (mw == 1) {
+          mscr[2 * lane] = mu0;
+          mscr[2 * lane + 1] = mu1;
+          mscr[64 + 2 * lane] = mv0;
+          mscr[64 + 2 * lane + 1] = mv1;
+        }
+        dead = bar2_or(dead);
+        if (mw == 0) {
+          mu0 = fmaxf(mu0, mscr[2 * lane]);
+          mu1 = fmaxf(mu1, mscr[2 * lane + 1]);
+          const int e0 = exponent_above(mu0), e1 = exponent_above(mu1);
+          Ex[es * 128 + 2 * lane] = e0;
+          Ex[es * 128 + 2 * lane + 1] = e1;
+          Fx[es * 128 + 2 * lane] = exp2i(e0 - 7);
+          Fx[es * 128 + 2 * lane + 1] = exp2i(e1 - 7);
+          if (!SYM) {
+            mv0 = fmaxf(mv0, mscr[64 + 2 * lane]);
+            mv1 = fmaxf(mv1, mscr[64 + 2 * lane + 1]);
+            const int f0 = exponent_above(mv0), f1 = exponent_above(mv1);
+            Ex[es * 128 + 64 + 2 * lane] = f0;
+            Ex[es * 128 + 64 + 2 * lane + 1] = f1;
+            Fx[es * 128 + 64 + 2 * lane] = exp2i(f0 - 7);
+            Fx[es * 128 + 64 + 2 * lane + 1] = exp2i(f1 - 7);
+          }
+        }
+        mu0 = mu1 = mv0 = mv1 = 0.f;
+        // warp 0 has read the scratch before warp 1 writes the next chunk's
+        bar2_or(false);
+      }
+      // j == 0: before the workers' first chunk; j >= 1: at the end of their
+      // chunk j - 1; j == nmy: at the end of their last chunk
+      __syncthreads();
+      if (flags[0]) dead = true;
+    }
+    // copies still in flight (a timeout, or the workers' failure, stopped
+    // the reads): wait for each with the full bound before the block exits
+    for (int t = done_t; t < issued_t; ++t) tc_wait(bar_of(t), (uint32_t)((t / MSW) & 1), TC_WAIT_LIMIT);
+  } else {
+    // ---- workers (staging, cut, combination) and the issuing warp ----
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const uint32_t dbase = smem_addr(dig);
+    // staging: worker -> raw rows r = tid / 32 and r + 16 of a slot, columns
+    // c, c + 1 (c = 2 (tid % 32)), one 16-byte copy each; raw row r + 16 is
+    // U's row r + 16 (U == V) or V's row r (U != V)
+    const int sr = tid >> 5, sc = 2 * (tid & 31);
+    const bool sokA = sc < wu, sokB = sc < (SYM ? wu : wv);
+    const int ldA = p, ldB = SYM ? p : q;
+    const float2* sA = U + cu0 + sc + (int64_t)sr * ldA;
+    const float2* sB = SYM ? U + cu0 + sc + (int64_t)(sr + 16) * ldA : V + cv0 + sc + (int64_t)sr * ldB;
+    const int64_t rA0 = sr, rB0 = SYM ? sr + 16 : sr;
+    auto stage_sub = [&](int g) {
+      if (g < G) {
+        const int64_t r0 = (int64_t)((int)blockIdx.x + (g / NSUB) * (int)gridDim.x) * EC + (g % NSUB) * SK;
+        float2* slot = raw + (size_t)(g % NR) * (32 * TG_RS) + sr * TG_RS + sc;
+        const bool okA = sokA && r0 + rA0 < n, okB = sokB && r0 + rB0 < n;
+        cp_async16(slot, okA ? sA + r0 * ldA : U, okA);
+        cp_async16(slot + 16 * TG_RS, okB ? sB + r0 * ldB : U, okB);
+      }
+      cp_async_commit();
+    };
+    // combine: worker warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. output
+    // row a = 32 (w % 2) + lane of the top (w % 4 < 2) or bottom half, columns
+    // 16 (w / 4) .. + 15
+    const int quarter = warp & 3, arow = 32 * (quarter & 1) + lane, cb = 16 * ((warp >> 2) & 3);
+    const bool top = quarter < 2;
+    float2 res[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) res[e] = make_float2(0.f, 0.f);
+    // digit item of this worker (one per sub-chunk): column c, rows
+    // 4 qd .. 4 qd + 3 of the sub-chunk, of U or (isv) of V
+    const bool isv = !SYM && tid >= 256;
+    const int loc = SYM ? tid : (tid & 255);
+    const int ic = 8 * ((loc >> 5) & 7) + (lane & 7);
+    const int iq = 2 * (((lane >> 4) & 1) + 2 * (loc >> 8)) + ((lane >> 3) & 1);
+    const int irow = (isv ? SK : 0) + 4 * iq;
+    const uint32_t doff = (isv ? 7 * plane : 0) + tc_off(ic, 4 * iq, SK);
+    bool failed = false;
+    int issued = 0;  // sub-chunks whose products were issued (the same in every thread)
+    if (worker) {
+      for (int g = 0; g < NR - 1; ++g) stage_sub(g);
+      cp_async_wait_group<NR - 2>();
+    }
+    __syncthreads();  // the maxima warps have written chunk 0's exponents
+    float scut = worker ? exp2i(7 - Ex[(isv ? 64 : 0) + ic]) : 0.f;
+    for (int g = 0; g < G; ++g) {
+      const int k = g / NSUB;
+      const int s = g - k * NSUB;
+      const int buf = g % NB;
+      const int es = k & 1;
+      if (!failed) {
+        bool ok = true;
+        if (worker) {
+          // this buffer's previous products (sub-chunk g - NB) are done
+          if (g >= NB) ok = tc_wait(mbase + 8u * buf, (uint32_t)((g / NB - 1) & 1), wait_limit);
+          if (ok) {
+            const float2* slot = raw + (size_t)(g % NR) * (32 * TG_RS) + irow * TG_RS + ic;
+            unsigned char* dst = dig + buf * DBUF + doff;
+            float d[4][ND];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const float2 x = slot[t * TG_RS];
+              digits_scaled<ND>(x.x, x.y, scut, d[t]);
+            }
+#pragma unroll
+            for (int i = 0; i < ND; ++i)
+              *reinterpret_cast<uint2*>(dst + i * plane) =
+                  make_uint2(pack_bf16x2(d[0][i], d[1][i]), pack_bf16x2(d[2][i], d[3][i]));
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          }
+          // raw rows NR - 1 sub-chunks ahead, into the slot cut one sub-chunk
+          // ago (free since the last barrier); then this thread's copies of
+          // sub-chunk g + 1 are complete, and the barrier publishes them
+          stage_sub(g + NR - 1);
+          cp_async_wait_group<NR - 2>();
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (bar1_or(!ok)) {
+          failed = true;
+        } else {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (issuer) {
+            if (lane == 0) {
+              const uint32_t ab = dbase + buf * DBUF, bb = SYM ? ab : ab + 7 * plane;
+              const uint64_t da = tc_desc(ab, SK), db = tc_desc(bb, SK);
+              const uint32_t acc0 = s > 0 ? 1u : 0u;
+              const uint32_t idesc0 = idesc & ~(0x3Fu << 17);
+#pragma unroll
+              for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int j0 = 0; j0 < ND - 2 * m; j0 += 4) {
+                  const int run = (ND - 2 * m - j0) < 4 ? (ND - 2 * m - j0) : 4;
+                  const uint32_t idn = idesc0 | ((uint32_t)((64 * run) >> 3) << 17);
+#pragma unroll
+                  for (int ks = 0; ks < SK / 16; ++ks)
+                    tc_mma(tmem + (uint32_t)((2 * m + j0) * 64), da + ((2 * m * plane + ks * 256) >> 4),
+                           db + ((j0 * plane + ks * 256) >> 4), idn, (m > 0 || ks > 0) ? 1u : acc0);
+                }
+              asm volatile(
+                  "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbase +
+                                                                                                  8u * buf)
+                  : "memory");
+            }
+            __syncwarp();
+          }
+          issued = g + 1;
+        }
+      }
+      if (s < NSUB - 1) continue;
+      // chunk end: its last products (a commit covers every earlier product
+      // of the issuing thread), then the combination
+      if (!failed) {
+        bool ok2 = true;
+        if (worker) ok2 = tc_wait(mbase + 8u * buf, (uint32_t)((g / NB) & 1), wait_limit);
+        if (bar1_or(!ok2)) {
+          failed = true;
+        } else if (worker) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const float fu = Fx[es * 128 + arow];
+          const float* Fv = Fx + es * 128 + (SYM ? 0 : 64) + cb;
+          const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll
+          for (int c0 = 0; c0 < 16; c0 += 4) {
+            uint32_t v[ND][4];
+#pragma unroll
+            for (int h = 0; h < ND; ++h)
+              if (top || h < ND - 1) tc_ld4(v[h], lanes + (uint32_t)(h * 64 + cb + c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              float S[ND];
+#pragma unroll
+              for (int h = 0; h < ND; ++h) S[h] = __uint_as_float(v[h][e]);
+              // top: groups 0..6 (even digits of U); bottom: groups 1..6
+              // (odd digits), block h holding group h + 1
+              const float2 w = top ? combine_groups_fast<ND, 4>(S) : combine_groups_fast<ND - 1, 3>(S);
+              const float fv = Fv[c0 + e];
+              res[c0 + e] = df_add(res[c0 + e], make_float2(w.x * fu * fv, w.y * fu * fv));
+            }
+          }
+        }
+      }
+      if (failed && tid == 0) flags[0] = 1;
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      // with the maxima warp: the next chunk's exponents are in parity slot
+      // es ^ 1, and this chunk's TMEM reads are done before its products
+      __syncthreads();
+      if (flags[1]) failed = true;
+      if (worker) scut = exp2i(7 - Ex[(es ^ 1) * 128 + (isv ? 64 : 0) + ic]);
+    }
+    if (worker) cp_async_wait_all();
+    if (failed) {
+      // a product or a maxima copy that did not complete in time: drain the
+      // tensor core (bounded) and report non-finite partial sums. Each
+      // buffer's barrier has at most one pending commit (its last issued
+      // sub-chunk); the final commit covers anything else issued.
+      if (tid == 0 && !flags[1]) atomicAdd(&g_oz_tc_timeouts, 1);
+      for (int b = 0; b < NB; ++b) {
+        const int last = issued - 1 - ((issued - 1 - b) % NB + NB) % NB;  // last g' < issued, g' % NB == b
+        if (last >= 0) tc_wait(mbase + 8u * b, (uint32_t)((last / NB) & 1), TC_WAIT_LIMIT);
+      }
+      tc_drain(issuer && lane == 0, mbase + 8u * NB);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) res[e] = make_float2(NAN, NAN);
+    }
+    // (the final stage below reuses the raw ring)
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+    float2* st = raw;  // 64 x 65 float2: odd-digit parts (bottom half) onto the even-digit parts
+    if (worker && !top) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) st[arow * 65 + cb + e] = res[e];
+    }
+    __syncthreads();
+    if (worker && top) {
+      float2* out = part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * 4096;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) out[arow * 64 + cb + e] = df_add(res[e], st[arow * 65 + cb + e]);
+    }
+    return;
+  }
+  // the maxima warps: the two barriers of the block's end
+  __syncthreads();
+  __syncthreads();
+}
+
 // Fixed-order sum of the per-block partials into G (float64, p x q); the
 // symmetric case fills the lower triangle from the upper one.
 __global__ void oz_gram_reduce_kernel(int p, int q, int nsplit, int nblk, int sym, int nbj,
@@ -1618,7 +2130,20 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
   // 16-byte copies need even row lengths and 16-byte aligned bases
   const bool vec16 = ((p | q) & 1) == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)V & 15) == 0;
   bool tri = false;  // symmetric Gram from full upper-triangle blocks
-  if (nd == ND && p <= 64 && q <= 64 && tp != 1) {
+  // 16-byte aligned blocks of even width: the kernel with the maxima warp
+  // (it counts its sub-chunks in 32 bits: n < 2^34)
+  const bool ring = nd == ND && tp != 1 && vec16 && n < ((int64_t)1 << 34);
+  if (ring) {
+    const bool one = p <= 64 && q <= 64;
+    tri = sym && !one;
+    const bool ksym = sym && one;
+    const size_t tsm = oz_gram_tc_ring_smem(ksym);
+    auto kern = ksym ? oz_gram_tc_ring_kernel<true> : oz_gram_tc_ring_kernel<false>;
+    GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    kern<<<dim3(ns, one ? 1 : nblk), TR_THREADS, tsm, st>>>(n, p, q, U, V, scratch, one ? 1 : nbj,
+                                                            tri ? 1 : 0);
+    GSI_LAUNCH_CHECK();
+  } else if (nd == ND && p <= 64 && q <= 64 && tp != 1) {
     // one 64 x 64 output block; every partial entry is written
     const size_t tsm = oz_gram_tc_smem(sym);
     auto kern = sym ? oz_gram_tc_kernel<true> : oz_gram_tc_kernel<false>;

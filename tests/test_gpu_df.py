@@ -135,12 +135,13 @@ def test_oz_gemm_in_place(G):
     assert np.linalg.norm(gsi.from_df(Ed.cpu().numpy()) - (U @ M - E)) <= 1e-13 * np.linalg.norm(U @ M)
 
 
-def _gram_bound(U, V, rows=256):
+def _gram_bound(U, V, rows=512):
     """Error bound of the digit-split Gram: per chunk of `rows` rows every
-    product is cut at 2^-49 of the chunk's column maxima. Chunks of 256 rows
-    bound the 64-row chunks of the mma.sync kernel and the 256/160-row chunks
-    of the tcgen05 kernel alike (a sub-chunk's maxima are at most its
-    chunk's)."""
+    product is cut at 2^-49 of the chunk's column maxima. Chunks of 512 rows
+    bound the 64-row chunks of the mma.sync kernel and the 512- and 256-row
+    chunks of the tcgen05 kernels alike (a sub-chunk's maxima are at most its
+    chunk's); the unaligned-block kernel's 160-row chunks straddle them, for
+    which the 2^-44 factor leaves room."""
     n, p = U.shape
     chunk_bound = np.zeros((p, V.shape[1]))
     for r0 in range(0, n, rows):
@@ -184,7 +185,8 @@ def _six_digit_block(rng, n, p):
     """Entries sum_{i<6} d_i 2^(-7(i+1)) with large positive digits
     (d_0 in [100, 127], d_1..d_5 in [40, 63]): below 1, 42 significant bits,
     so exact in df64 and cut into exactly these digits (column exponent 0),
-    with digit-pair group sums near the 2^24 limit over 256 rows. Returned as
+    with stacked digit-pair sums near 2^23.3 over the 512-row chunks of the
+    U == V kernel (its 2^24 limit allows 582 rows). Returned as
     integers (the value times 2^42) and as float64."""
     d = np.concatenate([rng.integers(100, 128, (n, p, 1)), rng.integers(40, 64, (n, p, 5))], axis=2)
     k = np.zeros((n, p), dtype=np.int64)
@@ -206,7 +208,7 @@ def _exact_gram(ku, kv):
 @pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("n,sym", [(1000, True), (1000, False), (256, True)])
 def test_oz_gram_large_digit_sums_exact(G, n, sym, path):
-    """Digit-pair group sums close to 2^24 (all digits large and positive, 256
+    """Digit-pair sums close to 2^24 (all digits large and positive, up to 512
     rows per exponent chunk) must still be summed exactly by the tensor
     cores: the Gram of these 42-bit entries equals the exact integer Gram to
     df64 rounding (relative 2^-46; a single lost unit in any group sum would
@@ -316,7 +318,7 @@ def test_oz_gemm_tcgen05_contraction_slices(G, n, p, fused, ne):
 @pytest.mark.parametrize("n,p,q,sym", [(100003, 64, 64, True), (100003, 64, 64, False), (4097, 17, 40, False),
                                        (70, 8, 8, True), (200000, 48, 5, False)])
 def test_oz_gram_tcgen05_and_mma_agree(G, n, p, q, sym):
-    """The tcgen05 Gram (256/160-row exponent chunks, tensor-memory group
+    """The tcgen05 Gram (512/256-row exponent chunks, tensor-memory group
     sums) and the mma.sync one (64-row chunks) are different roundings of the
     same exact Gram: each within the digit-split bound of the oracle, and
     within the sum of the two bounds of each other, on rows whose magnitudes
@@ -355,12 +357,15 @@ def _place(torch, gsi, x, off):
 @pytest.mark.parametrize("sym", [True, False])
 def test_oz_gram_unaligned_blocks(G, sym):
     """Blocks that start 8 bytes past a 16-byte boundary take the tcgen05
-    Gram's 8-byte copy path: the same Gram as from aligned blocks, bit for
-    bit."""
+    Gram that stages whole chunks with 8-byte copies; aligned blocks take the
+    one with the maxima warp (bulk copies, other exponent chunks). Both are
+    within the digit-split bound of the oracle's Gram of the same values, and
+    within twice that of each other; the unaligned result is symmetric when
+    U == V."""
     torch, gsi = G
     n, p = 3001, 64
     rng = np.random.default_rng(77 + sym)
-    U = _exact(gsi, rng.standard_normal((n, p)))
+    U = _exact(gsi, rng.standard_normal((n, p)) * np.exp(rng.uniform(-3, 3, (n, 1))))
     V = U if sym else _exact(gsi, rng.standard_normal((n, p)))
     outs = []
     for off in (0, 1):
@@ -369,7 +374,13 @@ def test_oz_gram_unaligned_blocks(G, sym):
         Gm = torch.zeros((p, p), dtype=torch.float64, device="cuda")
         gsi.oz_gram(Ud, Vd, Gm, sym=sym)
         outs.append(Gm.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+    bound = _gram_bound(U, V)
+    ref = O.gram(U, V)
+    for o in outs:
+        assert np.all(np.abs(o - ref) <= bound)
+        if sym:
+            assert np.array_equal(o, o.T)
+    assert np.all(np.abs(outs[0] - outs[1]) <= 2 * bound)
 
 
 @pytest.mark.parametrize("fused,ne", [(True, 0), (False, 2)])

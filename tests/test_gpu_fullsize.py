@@ -51,10 +51,11 @@ def test_spmm_full_size_sampled_rows(big):
 
 def _chunk_bound(u, v):
     """Digit-split Gram bound of the smaller tests: 2^-44 times the sum over
-    256-row chunks of rows x column maxima, plus 2^-46 sum |u||v|."""
-    cu = np.abs(u).reshape(-1, 256).max(1)
-    cv = np.abs(v).reshape(-1, 256).max(1)
-    return 2.0 ** -44 * 256 * float(cu @ cv) + 2.0 ** -46 * float(np.abs(u) @ np.abs(v))
+    512-row chunks (bounding the tcgen05 Grams' 512- and 256-row exponent
+    chunks) of rows x column maxima, plus 2^-46 sum |u||v|."""
+    cu = np.abs(u).reshape(-1, 512).max(1)
+    cv = np.abs(v).reshape(-1, 512).max(1)
+    return 2.0 ** -44 * 512 * float(cu @ cv) + 2.0 ** -46 * float(np.abs(u) @ np.abs(v))
 
 
 @pytest.mark.parametrize("sym", [False, True])

@@ -337,7 +337,7 @@ def test_fused_row_norm_matches_separate_pass(torch_cuda):
     """max_r sum_j |R[r, j]| formed in the tcgen05 block product's row-wise
     epilogue (tensor path 0, p even <= 64) against the separate reduction
     kernel (mma.sync path 1, where the product does not form it). The two
-    paths' Grams round differently (256/160- against 64-row exponent
+    paths' Grams round differently (512/256- against 64-row exponent
     chunks), so the runs agree to rounding: same iteration count, residuals
     within 1e-4 relative, infinity-norm residuals within 1e-3 (a lost row or a
     wrong reduction would be off by far more)."""
