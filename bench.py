@@ -44,7 +44,7 @@ GPU_ITERS_TO_TOL = {("cg", 128, 64): 4953}
 # elementwise terms; the CSR SpMM). None where a kernel changed after its
 # capture.
 NCU_TRAFFIC = {
-    "gram": {"n": 512000, "p": 64, "bytes": (2 * (262.231e6 + 3.466e6) + 3 * (524.441e6 + 3.660e6)) / 5},
+    "gram": {"n": 512000, "p": 64, "bytes": (2 * (264.358e6 + 3.413e6) + 3 * (532.697e6 + 3.756e6)) / 5},
     "blockmul": {"n": 512000, "p": 64, "bytes": (2 * (524.494e6 + 224.528e6) + 2 * (786.619e6 + 238.081e6)) / 4},
     "spmm": {"n": 512000, "p": 64, "bytes": 308.8e6 + 229.4e6},
 }
