@@ -1407,7 +1407,7 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
 constexpr int TR_WORKERS = 512;
 constexpr int TR_THREADS = TR_WORKERS + 96;  // + the issuing warp + two maxima warps
 constexpr int TR_BAR_COUNT = TR_WORKERS + 32;
-template <bool SYM>
+template <bool SYM, int NDT = ND>
 struct TrGeom {
   static constexpr int EC = SYM ? 512 : 256;       // exponent chunk rows
   static constexpr int SK = SYM ? 32 : 16;         // sub-chunk rows
@@ -1419,7 +1419,8 @@ struct TrGeom {
   static constexpr int MB = SYM ? 16 : 8;          // rows per operand in one maxima slot
   static constexpr int NMB = EC / MB;              // maxima batches per chunk
   static constexpr uint32_t PLANE = 64u * SK * 2;  // one digit plane: 64 columns x SK rows, bf16
-  static constexpr uint32_t DBUF = (SYM ? 8u : 14u) * PLANE;
+  // U == V: NDT planes and a zero pad plane; U != V: NDT planes of U, NDT of V
+  static constexpr uint32_t DBUF = (uint32_t)(SYM ? NDT + 1 : 2 * NDT) * PLANE;
   static constexpr size_t RAW_SLOT = (size_t)32 * TG_RS * sizeof(float2);
   static constexpr size_t MSLOT = (size_t)16 * 64 * sizeof(float2);  // 16 rows of 64 df64
   // raw slots, digit buffers, maxima slots, exponents and scales [2][128]
@@ -1436,7 +1437,10 @@ static_assert(TrGeom<false>::NR * TrGeom<false>::RAW_SLOT >= 64 * 65 * sizeof(fl
                   TrGeom<true>::NR * TrGeom<true>::RAW_SLOT >= 64 * 65 * sizeof(float2),
               "final stage fits the raw ring");
 
-size_t oz_gram_tc_ring_smem(bool sym) { return sym ? TrGeom<true>::smem() : TrGeom<false>::smem(); }
+size_t oz_gram_tc_ring_smem(bool sym, int nd) {
+  return nd == 3 ? (sym ? TrGeom<true, 3>::smem() : TrGeom<false, 3>::smem())
+                 : (sym ? TrGeom<true>::smem() : TrGeom<false>::smem());
+}
 
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() {
@@ -1465,11 +1469,11 @@ __device__ __forceinline__ bool bar1_or(bool v) {
   return r != 0;
 }
 
-template <bool SYM>
+template <bool SYM, int NDT>
 __global__ void __launch_bounds__(TR_THREADS, 1)
 oz_gram_tc_ring_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const float2* __restrict__ V,
                        float2* part, int nbj, int tri) {
-  using Geo = TrGeom<SYM>;
+  using Geo = TrGeom<SYM, NDT>;
   int bi = 0, bj = (int)blockIdx.y;
   if (tri) {
     int y = (int)blockIdx.y;
@@ -1505,7 +1509,7 @@ oz_gram_tc_ring_kernel(int64_t n, int p, int q, const float2* __restrict__ U, co
   if (SYM && worker)
     for (int e = tid; e < NB * (int)(plane / 16); e += TR_WORKERS) {
       const int b = e / (int)(plane / 16), o = e - b * (int)(plane / 16);
-      *reinterpret_cast<uint4*>(dig + b * DBUF + 7 * plane + 16 * o) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(dig + b * DBUF + NDT * plane + 16 * o) = make_uint4(0u, 0u, 0u, 0u);
     }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
@@ -1737,7 +1741,7 @@ oz_gram_tc_ring_kernel(int64_t n, int p, int q, const float2* __restrict__ U, co
     const int ic = 8 * ((loc >> 5) & 7) + (lane & 7);
     const int iq = 2 * (((lane >> 4) & 1) + 2 * (loc >> 8)) + ((lane >> 3) & 1);
     const int irow = (isv ? SK : 0) + 4 * iq;
-    const uint32_t doff = (isv ? 7 * plane : 0) + tc_off(ic, 4 * iq, SK);
+    const uint32_t doff = (isv ? NDT * plane : 0) + tc_off(ic, 4 * iq, SK);
     bool failed = false;
     int issued = 0;  // sub-chunks whose products were issued (the same in every thread)
     if (worker) {
@@ -1759,14 +1763,14 @@ oz_gram_tc_ring_kernel(int64_t n, int p, int q, const float2* __restrict__ U, co
           if (ok) {
             const float2* slot = raw + (size_t)(g % NR) * (32 * TG_RS) + irow * TG_RS + ic;
             unsigned char* dst = dig + buf * DBUF + doff;
-            float d[4][ND];
+            float d[4][NDT];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
               const float2 x = slot[t * TG_RS];
-              digits_scaled<ND>(x.x, x.y, scut, d[t]);
+              digits_scaled<NDT>(x.x, x.y, scut, d[t]);
             }
 #pragma unroll
-            for (int i = 0; i < ND; ++i)
+            for (int i = 0; i < NDT; ++i)
               *reinterpret_cast<uint2*>(dst + i * plane) =
                   make_uint2(pack_bf16x2(d[0][i], d[1][i]), pack_bf16x2(d[2][i], d[3][i]));
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1784,15 +1788,15 @@ oz_gram_tc_ring_kernel(int64_t n, int p, int q, const float2* __restrict__ U, co
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           if (issuer) {
             if (lane == 0) {
-              const uint32_t ab = dbase + buf * DBUF, bb = SYM ? ab : ab + 7 * plane;
+              const uint32_t ab = dbase + buf * DBUF, bb = SYM ? ab : ab + NDT * plane;
               const uint64_t da = tc_desc(ab, SK), db = tc_desc(bb, SK);
               const uint32_t acc0 = s > 0 ? 1u : 0u;
               const uint32_t idesc0 = idesc & ~(0x3Fu << 17);
 #pragma unroll
               for (int m = 0; m < 4; ++m)
 #pragma unroll
-                for (int j0 = 0; j0 < ND - 2 * m; j0 += 4) {
-                  const int run = (ND - 2 * m - j0) < 4 ? (ND - 2 * m - j0) : 4;
+                for (int j0 = 0; j0 < NDT - 2 * m; j0 += 4) {
+                  const int run = (NDT - 2 * m - j0) < 4 ? (NDT - 2 * m - j0) : 4;
                   const uint32_t idn = idesc0 | ((uint32_t)((64 * run) >> 3) << 17);
 #pragma unroll
                   for (int ks = 0; ks < SK / 16; ++ks)
@@ -1824,19 +1828,20 @@ oz_gram_tc_ring_kernel(int64_t n, int p, int q, const float2* __restrict__ U, co
           const uint32_t lanes = tmem + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll
           for (int c0 = 0; c0 < 16; c0 += 4) {
-            uint32_t v[ND][4];
+            uint32_t v[NDT][4];
 #pragma unroll
-            for (int h = 0; h < ND; ++h)
-              if (top || h < ND - 1) tc_ld4(v[h], lanes + (uint32_t)(h * 64 + cb + c0));
+            for (int h = 0; h < NDT; ++h)
+              if (top || h < NDT - 1) tc_ld4(v[h], lanes + (uint32_t)(h * 64 + cb + c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              float S[ND];
+              float S[NDT];
 #pragma unroll
-              for (int h = 0; h < ND; ++h) S[h] = __uint_as_float(v[h][e]);
+              for (int h = 0; h < NDT; ++h) S[h] = __uint_as_float(v[h][e]);
               // top: groups 0..6 (even digits of U); bottom: groups 1..6
               // (odd digits), block h holding group h + 1
-              const float2 w = top ? combine_groups_fast<ND, 4>(S) : combine_groups_fast<ND - 1, 3>(S);
+              const float2 w = top ? combine_groups_fast<NDT, (NDT > 4 ? 4 : NDT - 1)>(S)
+                                   : combine_groups_fast<NDT - 1, (NDT > 4 ? 3 : NDT - 2)>(S);
               const float fv = Fv[c0 + e];
               res[c0 + e] = df_add(res[c0 + e], make_float2(w.x * fu * fv, w.y * fu * fv));
             }
@@ -2130,15 +2135,19 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
   // 16-byte copies need even row lengths and 16-byte aligned bases
   const bool vec16 = ((p | q) & 1) == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)V & 15) == 0;
   bool tri = false;  // symmetric Gram from full upper-triangle blocks
-  // 16-byte aligned blocks of even width: the kernel with the maxima warp
-  // (it counts its sub-chunks in 32 bits: n < 2^34)
-  const bool ring = nd == ND && tp != 1 && vec16 && n < ((int64_t)1 << 34);
+  // 16-byte aligned blocks of even width: the kernel with the maxima warps
+  // (it counts its sub-chunks in 32 bits: n < 2^34). Its maxima warps copy
+  // a batch's rows in one piece where the block spans whole rows (p, q <=
+  // 64); 64-column blocks of wider matrices take one copy per row, where the
+  // whole-chunk kernel is as fast for 7 digits, so those stay with it.
+  const bool ring = tp != 1 && vec16 && n < ((int64_t)1 << 34) && ((p <= 64 && q <= 64) || nd == 3);
   if (ring) {
     const bool one = p <= 64 && q <= 64;
     tri = sym && !one;
     const bool ksym = sym && one;
-    const size_t tsm = oz_gram_tc_ring_smem(ksym);
-    auto kern = ksym ? oz_gram_tc_ring_kernel<true> : oz_gram_tc_ring_kernel<false>;
+    const size_t tsm = oz_gram_tc_ring_smem(ksym, nd);
+    auto kern = nd == 3 ? (ksym ? oz_gram_tc_ring_kernel<true, 3> : oz_gram_tc_ring_kernel<false, 3>)
+                        : (ksym ? oz_gram_tc_ring_kernel<true, ND> : oz_gram_tc_ring_kernel<false, ND>);
     GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
     kern<<<dim3(ns, one ? 1 : nblk), TR_THREADS, tsm, st>>>(n, p, q, U, V, scratch, one ? 1 : nbj,
                                                             tri ? 1 : 0);
