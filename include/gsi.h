@@ -432,18 +432,20 @@ gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, 
                                int32_t sym, double* G, void* stream);
 
 /* Which tensor-core kernels the digit-split products use: 0 (default) and 2
- * the tcgen05 kernels wherever they apply (7-digit Grams of any p, q <= 128
- * and the 7-digit dense apply, one CTA per 64 x 64 output block; 7-digit
- * block products of any p <= 128, the contraction cut into slices of at most
- * 64 for p > 64), 1 the mma.sync kernels everywhere (they also serve the
- * 3-digit products). Block products with p <= 64 are identical on both
- * (same digits, exact integer digit-pair sums, same combination order); for
- * p > 64 the tcgen05 slices take their own digit exponents and are summed in
- * df64, so the two agree to df64 rounding but not bit for bit.
- * Grams agree to float64-class accuracy but not bit for bit: the tcgen05
- * Gram takes its column exponents over 256-row (U == V, p <= 64) or 160-row
- * chunks,
- * the mma.sync Gram over 64-row chunks. The switch exists to compare them.
+ * the tcgen05 kernels wherever they apply (7-digit Grams of any p, q and
+ * the 7-digit dense apply, one CTA per 64 x 64 output block; 3-digit Grams
+ * and the 3-digit dense apply on 16-byte aligned blocks of even width;
+ * 7-digit block products of any p <= 128, the contraction cut into slices
+ * of at most 64 for p > 64), 1 the mma.sync kernels everywhere (they also
+ * serve the remaining 3-digit products). Block products with p <= 64 are
+ * identical on both (same digits, exact integer digit-pair sums, same
+ * combination order); for p > 64 the tcgen05 slices take their own digit
+ * exponents and are summed in df64, so the two agree to df64 rounding but
+ * not bit for bit. Grams agree to float64-class accuracy but not bit for
+ * bit: the tcgen05 Grams take their column exponents over 512-row (U == V)
+ * or 256-row chunks (aligned blocks of at most 64 columns, and 3 digits) or
+ * over 256-row (U == V) or 160-row chunks (the others), the mma.sync Gram
+ * over 64-row chunks. The switch exists to compare them.
  * Process-wide; the environment variable GSI_TENSOR_PATH=mma or =tcgen05
  * selects 1 or 2 before the first product. */
 gsi_status gsi_set_tensor_path(int32_t path);
