@@ -21,6 +21,12 @@ int sm_count();
 // Count of kernels launched by this library in this process.
 void note_launch();
 
+// cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+// only when the limit set for this kernel on the current device is below
+// bytes: the call costs microseconds of host time, which fall on the
+// critical path after every readback of the iteration.
+cudaError_t ensure_dyn_smem(const void* f, int bytes);
+
 }  // namespace gsi
 
 #define GSI_CUDA_TRY(expr)                                         \

@@ -34,6 +34,22 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   return fast_two_sum(s.x, s.y);
 }
 
+// acc += a b for a dot product: the product exact to ~2^-48 of |a b|
+// (TwoProd of the high words plus the cross terms), one TwoSum into acc's
+// high word, the low parts summed in float32; acc stays unnormalised (its
+// low word may exceed half an ulp of the high one) until df_acc_done. Half
+// the instructions of df_add(acc, df_mul(a, b)), for an error of about 2^-46
+// of the sum of |a b| per term.
+__device__ __forceinline__ void df_dot_acc(float2& acc, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+  const float2 t = two_sum(acc.x, p);
+  acc.x = t.x;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(t.y, e));
+}
+__device__ __forceinline__ float2 df_acc_done(float2 acc) { return two_sum(acc.x, acc.y); }
+
 // df + float
 __device__ __forceinline__ float2 df_add_f(float2 a, float b) {
   float2 s = two_sum(a.x, b);

@@ -369,8 +369,8 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
 #pragma unroll
           for (int m = 0; m < 2; ++m)  // constant indices keep the arguments in parameter space
             if (m < a.ne) y = df_add(y, df_mul(a.ce[m], a.E[m][idx]));
-          if (a.dot_self) dacc0 = df_add(dacc0, df_mul(y, y));
-          if (a.dot_with) dacc1 = df_add(dacc1, df_mul(y, a.dot_with[idx]));
+          if (a.dot_self) df_dot_acc(dacc0, y, y);
+          if (a.dot_with) df_dot_acc(dacc1, y, a.dot_with[idx]);
           a.out[idx] = y;
         }
       }
@@ -379,6 +379,8 @@ oz_gemm_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   cp_async_wait_all();
   if (a.dot_part) {
     __shared__ float2 red[2][GM_THREADS / 32];
+    dacc0 = df_acc_done(dacc0);  // the running sums were left unnormalised
+    dacc1 = df_acc_done(dacc1);
     for (int o = 16; o > 0; o >>= 1) {
       float2 t0 = make_float2(__shfl_xor_sync(0xffffffffu, dacc0.x, o), __shfl_xor_sync(0xffffffffu, dacc0.y, o));
       float2 t1 = make_float2(__shfl_xor_sync(0xffffffffu, dacc1.x, o), __shfl_xor_sync(0xffffffffu, dacc1.y, o));
@@ -728,12 +730,12 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
           y1 = df_add(y1, df_mul(a.ce[1], make_float2(e1.z, e1.w)));
         }
         if (a.dot_self) {
-          dacc0 = df_add(dacc0, df_mul(y0, y0));
-          dacc0 = df_add(dacc0, df_mul(y1, y1));
+          df_dot_acc(dacc0, y0, y0);
+          df_dot_acc(dacc0, y1, y1);
         }
         if (a.dot_with) {
-          dacc1 = df_add(dacc1, df_mul(y0, make_float2(w2.x, w2.y)));
-          dacc1 = df_add(dacc1, df_mul(y1, make_float2(w2.z, w2.w)));
+          df_dot_acc(dacc1, y0, make_float2(w2.x, w2.y));
+          df_dot_acc(dacc1, y1, make_float2(w2.z, w2.w));
         }
         if (lact) *reinterpret_cast<float4*>(a.out + R * p + 2 * lane) = make_float4(y0.x, y0.y, y1.x, y1.y);
         if (a.rinf_part) {  // this row's sum_j |hi(out[r, j])|, the same in every lane
@@ -754,8 +756,8 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
 #pragma unroll
       for (int m = 0; m < 2; ++m)  // constant indices keep the arguments in parameter space
         if (m < a.ne) y = df_add(y, df_mul(a.ce[m], a.E[m][idx]));
-      if (a.dot_self) dacc0 = df_add(dacc0, df_mul(y, y));
-      if (a.dot_with) dacc1 = df_add(dacc1, df_mul(y, a.dot_with[idx]));
+      if (a.dot_self) df_dot_acc(dacc0, y, y);
+      if (a.dot_with) df_dot_acc(dacc1, y, a.dot_with[idx]);
       a.out[idx] = y;
     }
     // the next tile rewrites Er and the digit planes: every warp leaves the
@@ -781,6 +783,8 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
   if (a.dot_part) {
     __shared__ float2 red[2][TC_THREADS / 32];
+    dacc0 = df_acc_done(dacc0);  // the running sums were left unnormalised
+    dacc1 = df_acc_done(dacc1);
     for (int o = 16; o > 0; o >>= 1) {
       float2 t0 = make_float2(__shfl_xor_sync(0xffffffffu, dacc0.x, o), __shfl_xor_sync(0xffffffffu, dacc0.y, o));
       float2 t1 = make_float2(__shfl_xor_sync(0xffffffffu, dacc1.x, o), __shfl_xor_sync(0xffffffffu, dacc1.y, o));
@@ -2052,7 +2056,7 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
       }
       b.rinf_part = last && rows ? rinf_part : nullptr;
       const size_t tsm = oz_gemm_tc_smem(K16h, NCmax);
-      GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+      GSI_CUDA_TRY(ensure_dyn_smem((const void*)oz_gemm_tc_kernel, (int)tsm));
       oz_gemm_tc_kernel<<<dim3(gx, ncs), TC_THREADS, tsm, st>>>(n, p, p16, K16h, b);
       GSI_LAUNCH_CHECK();
     }
@@ -2062,7 +2066,7 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
   GSI_LAUNCH_CHECK();
   size_t smem = oz_gemm_smem(K16, NCmax, fuse ? 2 : 1, nd);
   auto kern = nd == 3 ? oz_gemm_kernel<3> : oz_gemm_kernel<ND>;
-  GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GSI_CUDA_TRY(ensure_dyn_smem((const void*)kern, (int)smem));
   int64_t ntiles = (n + GM_RT - 1) / GM_RT;
   int per_sm = 1;
   GSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GM_THREADS, smem));
@@ -2148,7 +2152,7 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
     const size_t tsm = oz_gram_tc_ring_smem(ksym, nd);
     auto kern = nd == 3 ? (ksym ? oz_gram_tc_ring_kernel<true, 3> : oz_gram_tc_ring_kernel<false, 3>)
                         : (ksym ? oz_gram_tc_ring_kernel<true, ND> : oz_gram_tc_ring_kernel<false, ND>);
-    GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    GSI_CUDA_TRY(ensure_dyn_smem((const void*)kern, (int)tsm));
     kern<<<dim3(ns, one ? 1 : nblk), TR_THREADS, tsm, st>>>(n, p, q, U, V, scratch, one ? 1 : nbj,
                                                             tri ? 1 : 0);
     GSI_LAUNCH_CHECK();
@@ -2156,7 +2160,7 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
     // one 64 x 64 output block; every partial entry is written
     const size_t tsm = oz_gram_tc_smem(sym);
     auto kern = sym ? oz_gram_tc_kernel<true> : oz_gram_tc_kernel<false>;
-    GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    GSI_CUDA_TRY(ensure_dyn_smem((const void*)kern, (int)tsm));
     kern<<<ns, TG_THREADS, tsm, st>>>(n, p, q, U, V, vec16 ? 1 : 0, scratch, 1, 0);
     GSI_LAUNCH_CHECK();
   } else if (nd == ND && tp != 1) {
@@ -2165,14 +2169,14 @@ gsi_status oz_gram(int64_t n, int p, int q, const float2* U, const float2* V, bo
     // blocks only and is mirrored by the reduction
     tri = sym;
     const size_t tsm = oz_gram_tc_smem(false);
-    GSI_CUDA_TRY(cudaFuncSetAttribute(oz_gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    GSI_CUDA_TRY(ensure_dyn_smem((const void*)oz_gram_tc_kernel<false>, (int)tsm));
     oz_gram_tc_kernel<false><<<dim3(ns, nblk), TG_THREADS, tsm, st>>>(n, p, q, U, V, vec16 ? 1 : 0, scratch, nbj,
                                                                      tri ? 1 : 0);
     GSI_LAUNCH_CHECK();
   } else {
     size_t smem = oz_gram_smem(nd);
     auto kern = nd == 3 ? oz_gram_kernel<3> : oz_gram_kernel<ND>;
-    GSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GSI_CUDA_TRY(ensure_dyn_smem((const void*)kern, (int)smem));
     GSI_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)ns * nblk * 4096 * sizeof(float2), st));
     kern<<<dim3(ns, nblk), GR_THREADS, smem, st>>>(n, p, q, U, V, sym ? 1 : 0, nbj, scratch);
     GSI_LAUNCH_CHECK();

@@ -44,8 +44,7 @@ gsi_status small_step_df(int mode, int p, const double* C, const double* B, cons
   int use_smem = bytes <= 200 * 1024 ? 1 : (bytes - dfpart <= 200 * 1024 ? 2 : 0);
   size_t sm = use_smem == 1 ? bytes : use_smem == 2 ? bytes - dfpart : 0;
   if (use_smem)
-    GSI_CUDA_TRY(cudaFuncSetAttribute(small_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sm));
+    GSI_CUDA_TRY(ensure_dyn_smem((const void*)small_df_kernel, (int)sm));
   small_df_kernel<<<1, SD_THREADS, sm, st>>>(mode, p, C, B, Gam, Z, XX, XD, M, out,
                                              (unsigned char*)scratch, use_smem, (float2*)eig_ws);
   GSI_LAUNCH_CHECK();

@@ -23,6 +23,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "blas_f64.cuh"
@@ -44,6 +46,20 @@ gsi_status cuda_status(cudaError_t e) {
   set_last_error(cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return GSI_ERR_OOM;
   return GSI_ERR_CUDA;
+}
+
+cudaError_t ensure_dyn_smem(const void* f, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  int& cur = limit[{f, dev}];
+  if (cur >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 int sm_count() {
