@@ -443,7 +443,7 @@ gsi_status gsi_oz_gram_noalloc(int64_t n, int32_t p, int32_t q, const float* U, 
  * exponents and are summed in df64, so the two agree to df64 rounding but
  * not bit for bit. Grams agree to float64-class accuracy but not bit for
  * bit: the tcgen05 Grams take their column exponents over 512-row (U == V)
- * or 256-row chunks (aligned blocks of at most 64 columns, and 3 digits) or
+ * or 384-row chunks (aligned blocks of at most 64 columns, and 3 digits) or
  * over 256-row (U == V) or 160-row chunks (the others), the mma.sync Gram
  * over 64-row chunks. The switch exists to compare them.
  * Process-wide; the environment variable GSI_TENSOR_PATH=mma or =tcgen05

@@ -1394,8 +1394,8 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
 // of NR slots (16-byte cp.async, NR - 1 sub-chunks ahead; the rows come from
 // L2, where the maxima warp's read left them), cut them into NB digit
 // buffers with one mbarrier each, and combine once per chunk of EC rows
-// (512 for U == V, 256 otherwise; 256-row chunks keep U != V's two reads of
-// a row within L2 reach). Exactness of the accumulators: as for
+// (512 for U == V, 384 otherwise, which keeps U != V's two reads of a row
+// within L2 reach; 512 made them two DRAM reads). Exactness of the accumulators: as for
 // oz_gram_tc_kernel, 28800 EC < 2^24 for chunks of up to 582 rows.
 //
 // Roles: warps 0..15 stage, cut and combine; warp 16 issues the products;
@@ -1413,7 +1413,7 @@ constexpr int TR_THREADS = TR_WORKERS + 96;  // + the issuing warp + two maxima 
 constexpr int TR_BAR_COUNT = TR_WORKERS + 32;
 template <bool SYM, int NDT = ND>
 struct TrGeom {
-  static constexpr int EC = SYM ? 512 : 256;       // exponent chunk rows
+  static constexpr int EC = SYM ? 512 : 384;       // exponent chunk rows
   static constexpr int SK = SYM ? 32 : 16;         // sub-chunk rows
   static constexpr int NSUB = EC / SK;             // sub-chunks per chunk
   static constexpr int NB = 3;                     // digit buffers

@@ -34,14 +34,16 @@ def test_dense_apply(gsi, n, p, nd):
     gsi.oz_dense_apply(torch.from_numpy(gsi.to_df(A)).cuda(), torch.from_numpy(gsi.to_df(X)).cuda(), W, nd=nd)
     got = gsi.from_df(W.cpu().numpy())
     ref = A @ X
-    # per 256-row exponent chunk (the tcgen05 Gram's for U != V; the
-    # mma.sync kernel's 64-row chunks lie inside them): products cut at the
-    # chunk's column maxima
+    # per exponent chunk of the kernel that runs (the apply is a Gram of
+    # 64-column blocks of A: 3 digits on the maxima-warp kernel, 384-row
+    # chunks; 7 digits on the whole-chunk kernel, 160-row chunks): products
+    # cut at the chunk's column maxima
+    ec = 384 if nd == 3 else 160
     bound = np.zeros_like(ref)
-    for r0 in range(0, n, 256):
-        ca = np.abs(A[r0:r0 + 256]).max(0)     # column maxima of A^T's chunk = rows of A
-        cx = np.abs(X[r0:r0 + 256]).max(0)
-        bound += np.outer(ca, cx) * min(256, n - r0)
+    for r0 in range(0, n, ec):
+        ca = np.abs(A[r0:r0 + ec]).max(0)     # column maxima of A^T's chunk = rows of A
+        cx = np.abs(X[r0:r0 + ec]).max(0)
+        bound += np.outer(ca, cx) * min(ec, n - r0)
     scale = 2.0 ** -44 if nd == 7 else 2.0 ** -19
     assert np.all(np.abs(got - ref) <= scale * bound + 2.0 ** -46 * (np.abs(A) @ np.abs(X)))
 

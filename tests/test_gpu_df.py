@@ -135,13 +135,13 @@ def test_oz_gemm_in_place(G):
     assert np.linalg.norm(gsi.from_df(Ed.cpu().numpy()) - (U @ M - E)) <= 1e-13 * np.linalg.norm(U @ M)
 
 
-def _gram_bound(U, V, rows=512):
+def _gram_bound(U, V, rows=1536):
     """Error bound of the digit-split Gram: per chunk of `rows` rows every
-    product is cut at 2^-49 of the chunk's column maxima. Chunks of 512 rows
-    bound the 64-row chunks of the mma.sync kernel and the 512- and 256-row
-    chunks of the tcgen05 kernels alike (a sub-chunk's maxima are at most its
-    chunk's); the unaligned-block kernel's 160-row chunks straddle them, for
-    which the 2^-44 factor leaves room."""
+    product is cut at 2^-49 of the chunk's column maxima. Windows of 1536
+    rows hold whole exponent chunks of every kernel that may run (64 rows
+    for mma.sync; 512, 384 and 256 for the tcgen05 Grams), and a chunk's
+    maxima are at most its window's; the unaligned-block kernel's 160-row
+    chunks straddle them, for which the 2^-44 factor leaves room."""
     n, p = U.shape
     chunk_bound = np.zeros((p, V.shape[1]))
     for r0 in range(0, n, rows):
@@ -318,7 +318,7 @@ def test_oz_gemm_tcgen05_contraction_slices(G, n, p, fused, ne):
 @pytest.mark.parametrize("n,p,q,sym", [(100003, 64, 64, True), (100003, 64, 64, False), (4097, 17, 40, False),
                                        (70, 8, 8, True), (200000, 48, 5, False)])
 def test_oz_gram_tcgen05_and_mma_agree(G, n, p, q, sym):
-    """The tcgen05 Gram (512/256-row exponent chunks, tensor-memory group
+    """The tcgen05 Gram (512/384-row exponent chunks, tensor-memory group
     sums) and the mma.sync one (64-row chunks) are different roundings of the
     same exact Gram: each within the digit-split bound of the oracle, and
     within the sum of the two bounds of each other, on rows whose magnitudes

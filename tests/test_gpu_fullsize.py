@@ -51,11 +51,12 @@ def test_spmm_full_size_sampled_rows(big):
 
 def _chunk_bound(u, v):
     """Digit-split Gram bound of the smaller tests: 2^-44 times the sum over
-    512-row chunks (bounding the tcgen05 Grams' 512- and 256-row exponent
-    chunks) of rows x column maxima, plus 2^-46 sum |u||v|."""
-    cu = np.abs(u).reshape(-1, 512).max(1)
-    cv = np.abs(v).reshape(-1, 512).max(1)
-    return 2.0 ** -44 * 512 * float(cu @ cv) + 2.0 ** -46 * float(np.abs(u) @ np.abs(v))
+    1536-row windows (each holding whole 512- and 384-row exponent chunks of
+    the tcgen05 Grams) of rows x column maxima, plus 2^-46 sum |u||v|."""
+    b = 0.0
+    for r0 in range(0, u.shape[0], 1536):
+        b += float(np.abs(u[r0:r0 + 1536]).max() * np.abs(v[r0:r0 + 1536]).max()) * min(1536, u.shape[0] - r0)
+    return 2.0 ** -44 * b + 2.0 ** -46 * float(np.abs(u) @ np.abs(v))
 
 
 @pytest.mark.parametrize("sym", [False, True])
