@@ -1386,27 +1386,28 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
 // The kernel above stages a whole exponent chunk raw, which fills shared
 // memory and leaves room for two digit buffers only; its sub-chunk loop then
 // waits on the tensor core every other sub-chunk, and the chunk stays short.
-// Here the column exponents of a chunk come from a separate maxima warp that
-// reads the chunk's rows one chunk ahead of the workers: 1D bulk copies
+// Here the column exponents of a chunk come from two maxima warps that read
+// the chunk's rows one chunk ahead of the workers: 1D bulk copies
 // (cp.async.bulk, completion counted on an mbarrier per slot, no registers
-// held) of whole rows into a small ring of slots, reduced from shared memory.
-// The workers then stage the rows raw sub-chunk by sub-chunk through a ring
-// of NR slots (16-byte cp.async, NR - 1 sub-chunks ahead; the rows come from
-// L2, where the maxima warp's read left them), cut them into NB digit
-// buffers with one mbarrier each, and combine once per chunk of EC rows
-// (512 for U == V, 384 otherwise, which keeps U != V's two reads of a row
-// within L2 reach; 512 made them two DRAM reads). Exactness of the accumulators: as for
-// oz_gram_tc_kernel, 28800 EC < 2^24 for chunks of up to 582 rows.
+// held) of whole batches of rows into small per-warp rings of slots, reduced
+// from shared memory. The workers then stage the rows raw sub-chunk by
+// sub-chunk through a ring of NR slots (16-byte cp.async, NR - 1 sub-chunks
+// ahead; the rows come from L2, where the maxima warps' read left them), cut
+// them into NB digit buffers with one mbarrier each, and combine once per
+// chunk of EC rows (512 for U == V, 384 otherwise). Exactness of the
+// accumulators: as for oz_gram_tc_kernel, 28800 EC < 2^24 for chunks of up
+// to 582 rows.
 //
 // Roles: warps 0..15 stage, cut and combine; warp 16 issues the products;
-// warps 17 and 18 compute the maxima, each reducing half of every slot
-// (reading a chunk's rows costs one warp more issue slots than it gets
-// beside four busy workers), warp 17 also issuing the copies. Workers and the
-// issuing warp meet at named barrier 1 every sub-chunk, the maxima warps at
-// named barrier 2 every slot; all 19 warps meet at barrier 0 once per chunk,
-// where the maxima warps hand over the next chunk's exponents. Every thread
-// passes the same sequence of barrier-0 arrivals whatever fails: a timeout
-// only turns later work off (and the partial sums into NaN).
+// warps 17 and 18 compute the maxima, taking alternate batches, each with
+// its own ring and copies (reading a chunk's rows costs one warp more issue
+// slots than it gets beside four busy workers), and merge their maxima once
+// per chunk. Workers and the issuing warp meet at named barrier 1 every
+// sub-chunk, the maxima warps at named barrier 2 once per chunk; all 19
+// warps meet at barrier 0 once per chunk, where the maxima warps hand over
+// the next chunk's exponents. Every thread passes the same sequence of
+// barrier-0 arrivals whatever fails: a timeout only turns later work off
+// (and the partial sums into NaN).
 // ---------------------------------------------------------------------------
 constexpr int TR_WORKERS = 512;
 constexpr int TR_THREADS = TR_WORKERS + 96;  // + the issuing warp + two maxima warps
