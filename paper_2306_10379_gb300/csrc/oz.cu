@@ -1403,7 +1403,7 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
 // its own ring and copies (reading a chunk's rows costs one warp more issue
 // slots than it gets beside four busy workers), and merge their maxima once
 // per chunk. Workers and the issuing warp meet at named barrier 1 every
-// sub-chunk, the maxima warps at named barrier 2 once per chunk; all 19
+// sub-chunk, the maxima warps at named barrier 2 at each chunk's end; all 19
 // warps meet at barrier 0 once per chunk, where the maxima warps hand over
 // the next chunk's exponents. Every thread passes the same sequence of
 // barrier-0 arrivals whatever fails: a timeout only turns later work off
