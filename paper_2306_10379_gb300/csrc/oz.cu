@@ -495,6 +495,9 @@ __device__ __forceinline__ void tc_ld4(uint32_t r[4], uint32_t taddr) {
                : "r"(taddr));
 }
 
+// FUSED: the left operand is U0 + a1 U1 (a separate instantiation, so that
+// the fused load path's registers do not weigh on the other products)
+template <bool FUSED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   extern __shared__ __align__(16) unsigned char tc_smem[];
@@ -509,7 +512,7 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Fs + 64);  // [0] products, [1] drain
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool two = a.fuse_u1 != 0;
+  constexpr bool two = FUSED;
 
   // right operand digits (Md[plane][n][k]) into the core-matrix layout
   for (int e = tid; e < ND * NC * (K16 / 8); e += TC_THREADS) {
@@ -552,6 +555,28 @@ oz_gemm_tc_kernel(int64_t n, int p, int p16, int K16, OzGemmArgs a) {
   auto load_tile = [&](int64_t t) {
     const int64_t R = t * TC_M + rr;
     const bool live = t < ntiles && R < n;
+    const int64_t ob = R * a.ldu + a.kofs + 2 * j;  // the pair at k = 2 j
+    if (two && live && a.vec16 && a.kw >= 64 && (ob & 1) == 0) {
+      // the fused left sum over a full 64-column slice: each half-row's eight
+      // 16-byte loads (four of each operand) are issued before any of the
+      // df64 arithmetic that consumes them, so their latencies overlap
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float4 v[4], u[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          v[c] = *reinterpret_cast<const float4*>(a.U[0] + ob + 8 * (4 * h + c));
+          u[c] = *reinterpret_cast<const float4*>(a.U[1] + ob + 8 * (4 * h + c));
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          xr[2 * (4 * h + c)] = df_add(make_float2(v[c].x, v[c].y), df_mul(a.a1, make_float2(u[c].x, u[c].y)));
+          xr[2 * (4 * h + c) + 1] =
+              df_add(make_float2(v[c].z, v[c].w), df_mul(a.a1, make_float2(u[c].z, u[c].w)));
+        }
+      }
+      return;
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int k = 8 * c + 2 * j;
@@ -2057,8 +2082,9 @@ gsi_status oz_gemm(int64_t n, int p, int nk, const float2* const U[2], const dou
       }
       b.rinf_part = last && rows ? rinf_part : nullptr;
       const size_t tsm = oz_gemm_tc_smem(K16h, NCmax);
-      GSI_CUDA_TRY(ensure_dyn_smem((const void*)oz_gemm_tc_kernel, (int)tsm));
-      oz_gemm_tc_kernel<<<dim3(gx, ncs), TC_THREADS, tsm, st>>>(n, p, p16, K16h, b);
+      auto kern = b.fuse_u1 ? oz_gemm_tc_kernel<true> : oz_gemm_tc_kernel<false>;
+      GSI_CUDA_TRY(ensure_dyn_smem((const void*)kern, (int)tsm));
+      kern<<<dim3(gx, ncs), TC_THREADS, tsm, st>>>(n, p, p16, K16h, b);
       GSI_LAUNCH_CHECK();
     }
     return GSI_OK;
