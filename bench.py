@@ -44,8 +44,8 @@ GPU_ITERS_TO_TOL = {("cg", 128, 64): 4953}
 # elementwise terms; the CSR SpMM). None where a kernel changed after its
 # capture.
 NCU_TRAFFIC = {
-    "gram": {"n": 512000, "p": 64, "bytes": (2 * (264.358e6 + 3.413e6) + 3 * (532.697e6 + 3.756e6)) / 5},
-    "blockmul": {"n": 512000, "p": 64, "bytes": (2 * (524.699e6 + 224.487e6) + 2 * (786.622e6 + 237.716e6)) / 4},
+    "gram": {"n": 512000, "p": 64, "bytes": (2 * (263.393e6 + 3.634e6) + 3 * (936.391e6 + 3.764e6)) / 5},
+    "blockmul": {"n": 512000, "p": 64, "bytes": (2 * (524.536e6 + 224.654e6) + 2 * (786.669e6 + 238.069e6)) / 4},
     "spmm": {"n": 512000, "p": 64, "bytes": 308.8e6 + 229.4e6},
 }
 TRAFFIC_SOURCE = "one-kernel ncu captures at 80^3 (n = 512,000, p = 64), scaled by rows"

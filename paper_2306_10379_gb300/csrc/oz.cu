@@ -1419,7 +1419,8 @@ oz_gram_tc_kernel(int64_t n, int p, int q, const float2* __restrict__ U, const f
 // sub-chunk through a ring of NR slots (16-byte cp.async, NR - 1 sub-chunks
 // ahead; the rows come from L2, where the maxima warps' read left them), cut
 // them into NB digit buffers with one mbarrier each, and combine once per
-// chunk of EC rows (512 for U == V, 384 otherwise). Exactness of the
+// chunk of EC rows (512 for U == V, 384 otherwise: there part of the second
+// reads already miss L2, but the fewer combinations pay for it). Exactness of the
 // accumulators: as for oz_gram_tc_kernel, 28800 EC < 2^24 for chunks of up
 // to 582 rows.
 //
